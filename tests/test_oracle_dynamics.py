@@ -1,0 +1,247 @@
+"""Pins of the oracle's time stepping against closed forms, invariants and
+textbook special cases (no GPU).
+
+* conservation: periodic lattices keep mass, momentum and (thermal mode)
+  energy to round-off -- the forcing moments are antisymmetric differences;
+* isothermal sound (Sec. III.B): damping gamma = k^2 eta / rho0 (Eq. 99) with
+  eta = rho T tau (Eq. 84) and omega^2 = k^2 T - gamma^2 (Eq. 101), on the
+  1D 256-site wave and on the paper's D3Q19 80-cell box at T = 0.05, 0.2, 0.4;
+* shear waves: transverse momentum decays at eta k^2 / rho0 (Eq. 84), along an
+  axis and along a diagonal (isotropy);
+* dimensional collapse: a D3Q19 run uniform in z equals the D2Q9 run, which
+  ties the derived D2Q9 / D1Q3 equilibria, forcing and gradient to the printed
+  D3Q19 ones;
+* standard-lattice limit: at T = c^2/3 and small amplitude the scheme is the
+  textbook D1Q3 BGK with relaxation time tau + 1/2, to O(amplitude^2);
+* thermal mode: 1D adiabatic sound speed sqrt(3 T) (gamma = (d+2)/d = 3), and
+  two-state Riemann data converge toward the exact gamma = 3 Euler solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _physics import (exact_riemann, fit_damped_mode, fit_exponential, mode_amplitude,
+                      standard_d1q3_bgk)
+from paper_2501_00620_gb300 import workloads as W
+
+
+def rel(d0, d1):
+    return np.abs(d1 - d0) / np.abs(d0[0])
+
+
+@pytest.mark.parametrize("d,shape", [(1, (1, 1, 64)), (2, (1, 12, 16)), (3, (6, 5, 8))])
+def test_conservation_thermal(d, shape):
+    rng = np.random.default_rng(d)
+    nz, ny, nx = shape
+    s = oracle.Sim(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True)
+    rho = 1 + 0.1 * rng.normal(size=shape)
+    u = 0.05 * rng.normal(size=(d,) + shape)
+    T = 0.1 * (1 + 0.1 * rng.normal(size=shape))
+    s.init(rho, u, T)
+    d0 = s.diagnostics()
+    s.step(100)
+    d1 = s.diagnostics()
+    assert rel(d0, d1)[: d + 1].max() < 1e-13          # mass, momentum
+    assert abs(d1[-1] - d0[-1]) / abs(d0[-1]) < 1e-12   # energy
+    # a plausible mistake -- dropping the (dt/2) G term from T -- breaks energy
+    # conservation by orders of magnitude more than this bound (see the
+    # isothermal run below, which relaxes energy and is not conservative).
+
+
+def test_isothermal_is_not_energy_conserving():
+    """Control for the energy bound above: with T fixed the collision relaxes
+    the second-moment trace towards d rho T0, so energy drifts."""
+    rng = np.random.default_rng(1)
+    s = oracle.Sim(1, 64, tau=0.6, T0=0.1, thermal=False)
+    s.init(1 + 0.1 * rng.normal(size=(1, 1, 64)), 0.05 * rng.normal(size=(1, 1, 1, 64)),
+           0.1 * (1 + 0.1 * rng.normal(size=(1, 1, 64))))
+    d0 = s.diagnostics()
+    s.step(100)
+    d1 = s.diagnostics()
+    assert rel(d0, d1)[:2].max() < 1e-13
+    assert abs(d1[-1] - d0[-1]) / abs(d0[-1]) > 1e-6
+
+
+def sound_run(d, N, T0, tau, steps, amp, thermal=False, isentropic=False):
+    if d == 1:
+        s = oracle.Sim(1, N, tau=tau, T0=T0, thermal=thermal)
+        shape = (1, 1, N)
+        coord = np.arange(N)[None, None, :]
+    else:  # the paper's geometry: wave along z in a D3Q19 box, uniform in x, y
+        s = oracle.Sim(3, 1, 1, N, tau=tau, T0=T0, thermal=thermal)
+        shape = (N, 1, 1)
+        coord = np.arange(N)[:, None, None]
+    k = 2 * np.pi / N
+    rho = 1 + amp * np.sin(k * coord) * np.ones(shape)
+    T = T0 * (1 + 2 * (rho - 1)) if isentropic else T0
+    s.init(rho, np.zeros((d,) + shape), T)
+    ts, a = [], []
+    for t in range(steps + 1):
+        r, _, _ = s.moments()
+        ts.append(t)
+        a.append(mode_amplitude(r - 1, k, coord))
+        s.step(1)
+    g, w = fit_damped_mode(np.array(ts, float), np.array(a), k * k * T0 * tau, k * np.sqrt(T0))
+    return k, g, w
+
+
+def test_sound_wave_1d_closed_form():
+    """1D sound wave, T0 = 1/3, tau = 0.8, 256 sites, 2000 steps: Eqs. 99, 101."""
+    k, g, w = sound_run(1, 256, 1 / 3, 0.8, 2000, 1e-3)
+    g_ref = k * k * (1 / 3) * 0.8
+    w_ref = np.sqrt(k * k / 3 - g_ref ** 2)
+    assert abs(g / g_ref - 1) < 5e-3
+    assert abs(w / w_ref - 1) < 5e-3
+
+
+def test_sound_wave_d3q19_vs_temperature():
+    """The paper's Fourier analysis (Sec. III.B): D3Q19, k = 2 pi / 80,
+    A = 1e-4, eta = 0.125 at T = 0.05, 0.2, 0.4.  gamma = k^2 eta (Eq. 99)
+    within 1%, and the slope of omega^2 + gamma^2 against T equals k^2 within
+    1% (the paper prints 0.006153 against 0.006169)."""
+    eta = 0.125
+    Ts, y = [0.05, 0.2, 0.4], []
+    for T in Ts:
+        k, g, w = sound_run(3, 80, T, eta / T, 1500, 1e-4)
+        assert abs(g / (k * k * eta) - 1) < 1e-2
+        y.append(w * w + g * g)
+    slope = np.polyfit(Ts, y, 1)[0]
+    assert abs(slope / (k * k) - 1) < 1e-2
+    # T >= 0.2: each point individually within 1% of k^2 T (Eq. 101)
+    assert abs(y[1] / (k * k * 0.2) - 1) < 1e-2 and abs(y[2] / (k * k * 0.4) - 1) < 1e-2
+
+
+def test_sound_dispersion_error_is_second_order():
+    """At T = 0.05 the deviation of omega^2 + gamma^2 from k^2 T is a lattice
+    error: it falls by 4x when k halves (second-order accuracy, Sec. II.C)."""
+    errs = []
+    for N in (80, 160):
+        k, g, w = sound_run(1, N, 0.05, 2.5, 15 * N + 300, 1e-4)
+        errs.append((w * w + g * g) / (k * k * 0.05) - 1)
+    ratio = errs[0] / errs[1]
+    assert 3.6 < ratio < 4.4
+
+
+@pytest.mark.parametrize("d,shape", [(2, (1, 4, 64)), (3, (2, 2, 64))])
+def test_shear_wave_axis(d, shape):
+    """u_y = A sin(kx) decays at rate (eta/rho) k^2 = T tau k^2 (Eq. 84)."""
+    T, tau = 0.2, 0.8
+    nz, ny, nx = shape
+    s = oracle.Sim(d, nx, ny, nz, tau=tau, T0=T)
+    k = 2 * np.pi / nx
+    x = np.arange(nx)[None, None, :] * np.ones(shape)
+    u = np.zeros((d,) + shape)
+    u[1] = 1e-3 * np.sin(k * x)
+    s.init(1.0, u, T)
+    ts, a = [], []
+    for t in range(301):
+        _, uu, _ = s.moments()
+        ts.append(t)
+        a.append(mode_amplitude(uu[1], k, x))
+        s.step(1)
+    g = fit_exponential(np.array(ts, float), np.array(a))
+    assert abs(g / (T * tau * k * k) - 1) < 5e-3
+
+
+def test_shear_wave_diagonal_isotropy():
+    """Shear wave along (1,1) on D2Q9: same viscosity as along an axis."""
+    T, tau, n = 0.2, 0.8, 64
+    s = oracle.Sim(2, n, n, 1, tau=tau, T0=T)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    k = 2 * np.pi / n
+    ph = k * (x + y)
+    u = np.zeros((2, 1, n, n))
+    u[0, 0] = -1e-3 * np.sin(ph) / np.sqrt(2)
+    u[1, 0] = 1e-3 * np.sin(ph) / np.sqrt(2)
+    s.init(1.0, u, T)
+    ts, a = [], []
+    for t in range(201):
+        _, uu, _ = s.moments()
+        ts.append(t)
+        a.append(2 * np.mean((-uu[0, 0] + uu[1, 0]) / np.sqrt(2) * np.sin(ph)))
+        s.step(1)
+    g = fit_exponential(np.array(ts, float), np.array(a))
+    assert abs(g / (T * tau * 2 * k * k) - 1) < 1e-2
+
+
+@pytest.mark.parametrize("lo", [1, 2])
+def test_dimensional_collapse(lo):
+    """Isothermal: D3Q19 uniform in z == D2Q9; D2Q9 uniform in y == D1Q3."""
+    rng = np.random.default_rng(lo)
+    nx, ny = 16, (8 if lo == 2 else 1)
+    rho = 1 + 0.05 * rng.normal(size=(1, ny, nx))
+    u = 0.05 * rng.normal(size=(lo, 1, ny, nx))
+    s_lo = oracle.Sim(lo, nx, ny if lo == 2 else 1, 1, tau=0.7, T0=0.2)
+    s_lo.init(rho, u, 0.2)
+    u_hi = np.zeros((lo + 1, 1, ny, nx))
+    u_hi[:lo] = u
+    s_hi = oracle.Sim(lo + 1, nx, ny, 1, tau=0.7, T0=0.2)
+    s_hi.init(rho, u_hi, 0.2)
+    s_lo.step(50)
+    s_hi.step(50)
+    r_lo, uu_lo, _ = s_lo.moments()
+    r_hi, uu_hi, _ = s_hi.moments()
+    assert abs(r_lo - r_hi).max() < 1e-13
+    assert abs(uu_lo - uu_hi[:lo]).max() < 1e-13
+    assert abs(uu_hi[lo]).max() < 1e-15
+
+
+def test_standard_lattice_limit():
+    """T = c^2/3 (zero bump width at rest), amplitude 1e-3: the scheme agrees
+    with the textbook D1Q3 BGK at tau_LB = tau + 1/2 to O(A^2); the other
+    common tau convention (tau_LB = tau) is far away."""
+    N, A, tau = 256, 1e-3, 0.8
+    rho0 = 1 + A * np.sin(2 * np.pi * np.arange(N) / N)
+    ref = standard_d1q3_bgk(rho0, np.zeros(N), tau + 0.5, 2000, {500, 2000})
+    wrong = standard_d1q3_bgk(rho0, np.zeros(N), tau, 2000, {2000})
+    s = oracle.Sim(1, N, tau=tau, T0=1 / 3)
+    s.init(rho0[None, None, :], np.zeros((1, 1, 1, N)), 1 / 3)
+    s.step(500)
+    r, _, _ = s.moments()
+    assert abs(r[0, 0] - ref[500]).max() < 10 * A * A
+    s.step(1500)
+    r, _, _ = s.moments()
+    assert abs(r[0, 0] - ref[2000]).max() < 10 * A * A
+    assert abs(r[0, 0] - wrong[2000]).max() > 1e-5
+
+
+def test_thermal_sound_speed():
+    """Thermal mode, 1D isentropic wave (dT/T = 2 drho/rho): omega = k sqrt(3 T0)."""
+    k, g, w = sound_run(1, 256, 0.1, 0.8, 2000, 1e-4, thermal=True, isentropic=True)
+    assert abs(w / (k * np.sqrt(3 * 0.1)) - 1) < 2e-3
+
+
+def test_riemann_converges_to_exact_gamma3():
+    """Two-state Riemann data of config 2 (rho 1 : 0.125, T 1.0 : 0.8 in units
+    of 0.12 c^2, tau = 0.55, fixed-state ends): the L1 error against the exact
+    gamma = 3 solution falls with resolution (steps = N/2, before any wave
+    reaches a reservoir), and gamma = 3 fits far better than gamma = 5/3."""
+    Tu = W.T_UNIT_RIEMANN
+    L, R = (1.0, 0.0, Tu), (0.125, 0.0, 0.125 * 0.8 * Tu)
+    errs, errs_wrong_gamma = [], []
+    for N in (256, 512, 1024):
+        rho, u, T = W.riemann_1d(N, Tu)
+        s = oracle.Sim(1, N, tau=0.55, T0=Tu, thermal=True, bc="fixed")
+        s.init(rho, u, T)
+        steps = N // 2
+        s.step(steps)
+        r, uu, TT = s.moments()
+        xi = (np.arange(N) + 0.5 - N // 2) / steps
+        re, ue, pe = exact_riemann(L, R, 3.0, xi)
+        errs.append((np.mean(abs(r[0, 0] - re)), np.mean(abs(uu[0, 0] - ue)),
+                     np.mean(abs(r[0, 0] * TT[0, 0] - pe))))
+        rw, _, _ = exact_riemann(L, R, 5.0 / 3.0, xi)
+        errs_wrong_gamma.append(np.mean(abs(r[0, 0] - rw)))
+    errs = np.array(errs)
+    assert (np.diff(errs, axis=0) < 0).all()
+    assert errs[-1, 0] < 0.6 * errs[0, 0] and errs[-1, 1] < 0.4 * errs[0, 1]
+    assert errs[-1, 0] < 0.5 * errs_wrong_gamma[-1]
+
+
+def test_fixed_state_uniform_is_steady():
+    """Fixed-state reservoirs equal to a uniform interior leave it at rest."""
+    s = oracle.Sim(2, 12, 5, 1, tau=0.55, T0=0.12, thermal=True, bc="fixed")
+    s.init(1.0, np.zeros((2, 1, 5, 12)), 0.12)
+    s.step(20)
+    r, u, T = s.moments()
+    assert abs(r - 1).max() < 1e-14 and abs(u).max() < 1e-14 and abs(T - 0.12).max() < 1e-14
