@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the fused bump-function LBM step on GB300.
+
+One step = one pass of the whole hot path over the lattice: pull streaming,
+moments, isotropic-gradient corrections, equilibrium + forcing, BGK, store,
+and the FP64 mass/momentum/energy reduction of the state (recorded every
+step).  Default workload: the 3D periodic D3Q19 256^3 solenoidal-turbulence
+configuration in FP32 (the paper's own lattice, and the largest single-GPU
+configuration); --workload tgv2d | sound1d | riemann1d select the others.
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+copy of the workload (independent replicas, weak scaling, no collective on
+the data path); timing is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline at stated error vs FP64 oracle; serving p50/p99"
+
+WORKLOAD_TEXT = {
+    "turb3d": "D3Q19 256^3 periodic; seeded solenoidal u, E(k)~k^4 exp(-2k^2/k0^2), k0=8, "
+              "Mach_rms 0.3; rho=1, T=T0=0.05; tau=0.52; isothermal",
+    "tgv2d": "D2Q9 2048^2 periodic; Taylor-Green u0=0.1 + Gaussian rho/T pulse (amp 0.2, sigma 64); "
+             "T0=0.1; tau=0.6; thermal",
+    "sound1d": "D1Q3 256 periodic sound wave, rho=1+1e-3 sin(2 pi x/256), T0=1/3, tau=0.8; isothermal",
+    "riemann1d": "D1Q3 4096 two-state Riemann (rho 1:0.125, T 1.0:0.8 x 0.15), tau=0.55; thermal; "
+                 "fixed-state ends",
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="turb3d", choices=sorted(WORKLOAD_TEXT))
+    p.add_argument("--dtype", default=None, help="storage dtype override: f64 f32 f16 bf16")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(dev):
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+def algorithmic_bytes_per_site(d, dtype):
+    Q = {1: 3, 2: 9, 3: 19}[d]
+    NB = {1: 1, 2: 3, 3: 6}[d]
+    fb = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[dtype]
+    bb = 8 if dtype == "f64" else 4
+    return 2 * (Q * fb + NB * bb)   # read + write of the emitted state
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_step.cuh", "lbm_lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_00620_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, dtype):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if it was captured from the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_%s_%s.md" % (workload, dtype))
+    try:
+        text = open(p).read()
+    except OSError:
+        return None
+    vals = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+
+def workload_params(name, dtype_override):
+    from paper_2501_00620_gb300 import workloads as W
+    c = dict(W.CONFIGS[name])
+    if dtype_override:
+        c["dtype"] = dtype_override
+    return c
+
+
+def oracle_sample(name, budget_s, steps_total):
+    """A bounded sample of the workload for the CPU oracle: a smaller lattice
+    of the same generator, sized so that steps_total steps take ~budget_s."""
+    import numpy as np
+    import oracle
+    from paper_2501_00620_gb300 import workloads as W
+    c = W.CONFIGS[name]
+    d = c["d"]
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    # probe the oracle's rate on a small instance
+    n_probe = {1: 4096, 2: 64, 3: 16}[d]
+    sites_probe = n_probe ** (1 if d == 1 else d)
+    rho, u, T = W.fields_for(name, scale=n_probe) if d > 1 else W.fields_for(name)
+    if d == 1:
+        sites_probe = c["nx"]
+        n_probe = c["nx"]
+    s = oracle.Sim(d, n_probe, n_probe if d >= 2 else 1, n_probe if d == 3 else 1, tau=c["tau"], T0=c["T0"],
+                   thermal=c["thermal"], bc=c["bc"])
+    s.init(rho, u, T)
+    t0 = time.perf_counter()
+    s.step(2)
+    rate = 2 * sites_probe / (time.perf_counter() - t0)
+    if d == 1:
+        return n_probe, threads, rate
+    # at most 2M sites: the oracle keeps ~70 doubles per site
+    target_sites = max(sites_probe, min(2.0e6, rate * budget_s / max(steps_total, 1)))
+    n = int(target_sites ** (1.0 / d))
+    n = max(8, min(n, c["nx"]))
+    return n, threads, rate
+
+
+def run_oracle(name, n, steps, warmup):
+    import oracle
+    from paper_2501_00620_gb300 import workloads as W
+    c = W.CONFIGS[name]
+    d = c["d"]
+    rho, u, T = W.fields_for(name, scale=n) if d > 1 else W.fields_for(name)
+    s = oracle.Sim(d, n, n if d >= 2 else 1, n if d == 3 else 1, tau=c["tau"], T0=c["T0"],
+                   thermal=c["thermal"], bc=c["bc"])
+    s.init(rho, u, T)
+    s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    sites = n ** d if d > 1 else n
+    return sites * steps / dt / 1e6, dt, sites
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    name = args.workload
+    c = workload_params(name, None)
+    n, threads, _ = oracle_sample(name, 120.0, args.steps + args.warmup)
+    mlups, dt, sites = run_oracle(name, n, args.steps, args.warmup)
+    d = c["d"]
+    sample = ("%s sample: same generator on %s (%d sites), %d timed steps after %d warm-up"
+              % (name, "x".join([str(n)] * d) if d > 1 else str(n), sites, args.steps, args.warmup))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": name + ": " + WORKLOAD_TEXT[name], "reference": "FP64 CPU oracle (oracle/)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2501_00620_gb300 import lbm
+    from paper_2501_00620_gb300 import workloads as W
+
+    name = args.workload
+    c = workload_params(name, args.dtype)
+    d, nx, ny, nz = c["d"], c["nx"], c["ny"], c["nz"]
+    N = nx * ny * nz
+    rho, u, T = W.fields_for(name)
+
+    stream = torch.cuda.Stream(device=local)
+    sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=c["dtype"],
+                         thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True)
+    sim.init(rho, u, T)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (includes autotuning and graph capture)
+    sim.step(max(args.warmup, 3))
+    sim.sync()
+    barrier()
+
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    sim.sync()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    ms_per_step = ms_max / args.steps
+
+    # roofline of the step kernel (one launch per step)
+    bps = algorithmic_bytes_per_site(d, c["dtype"])
+    achieved = N * bps / (ms_per_step * 1e-3) / 1e9
+    peak, peak_src = hbm_peak()
+    traffic = profiled_traffic(name, c["dtype"])
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hr, hu, hT = pin(rho), pin(u), pin(T)
+        orr = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        ou = torch.empty(d * N, dtype=torch.float64).pin_memory().numpy()
+        oT = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        rec = np.empty(d + 3)
+        barrier()
+        t0 = time.perf_counter()
+        lbm.lbm_init(sim.h, hr, hu, hT)
+        for _ in range(args.steps):
+            lbm.lbm_step(sim.h, 1)
+            lbm.lbm_last_diagnostics(sim.h, rec)
+        lbm.lbm_moments(sim.h, orr, ou, oT)
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        h2d = (2 + d) * N * 8
+        d2h = (d + 3) * 8 * args.steps + (2 + d) * N * 8
+        e2e = {"value": world * N * args.steps / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "lbm_init from pinned host fields, per step lbm_step(1) + lbm_last_diagnostics "
+                           "(d+3 doubles D2H), final lbm_moments (rho, u, T D2H)"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n, threads, _ = oracle_sample(name, 15.0, 4)
+        steps_cpu = 4 if d > 1 else 200
+        mlups, dt, sites = run_oracle(name, n, steps_cpu, 1)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "%s on %d sites (%s), %d steps, %.1f s" % (
+                   name, sites, "x".join([str(n)] * d) if d > 1 else str(n), steps_cpu, dt)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if c["dtype"] == "f64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": name + ": " + WORKLOAD_TEXT[name], "storage": c["dtype"],
+                   "sites": N, "l2": "state of %.2f GB per buffer > 129 MB L2, no flush needed"
+                   % (N * bps / 2 / 1e9) if N * bps / 2 > 2 * 129e6 else "flush not applied: small lattice",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_src, "bytes_per_site": bps, "kernel": "step_kernel"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the bump-function lattice
+ * Boltzmann method of Afrasiabian & Denniston, "A Novel Velocity
+ * Discretization for Lattice Boltzmann Method: Application to Compressible
+ * Flow" (arXiv 2501.00620).
+ *
+ * The method (Sec. II.B-C): every discrete population f_i is a bump in velocity
+ * space with mean e_i and a per-site variance tensor b (Eq. 23), which lets the
+ * equilibrium match the Maxwell-Boltzmann moments through third order on the
+ * nearest-neighbour lattices D1Q3, D2Q9 and D3Q19 (Eqs. 28-31, Appendix A).
+ * One time step takes the moments of the auxiliary populations fbar and of
+ * bbar, corrects the velocity with an isotropic finite-difference gradient of
+ * rho*b (Eqs. 57, 59, 67-68), relaxes fbar with forcing (Eq. 55) and bbar
+ * (Eqs. 63, 65), and streams fbar (Eq. 49) and the mass-weighted bbar (Eq. 66)
+ * to the nearest neighbours.
+ *
+ * Conventions for every entry point:
+ *  - Lattice units: dx = dt = c = 1.  tau is the continuous relaxation time of
+ *    Sec. II.C, so the discrete relaxation factor is omega = 1/(tau + 1/2)
+ *    (Eq. 55) and the shear viscosity is eta = rho T tau (Eq. 84).
+ *  - Sites are numbered s = x + nx*(y + ny*z).  Scalar fields are arrays of N
+ *    doubles; vector fields are d planes of N doubles (component a of site s
+ *    at a*N + s); symmetric tensors (b) are nb planes in the component order
+ *    1D (xx), 2D (xx, yy, xy), 3D (xx, yy, zz, xy, xz, yz).
+ *  - Population order: D3Q19 is the column order of the transformation matrix
+ *    of Appendix B (rest, +x, +y, -x, -y, +z, -z, then the 12 edge
+ *    velocities); D2Q9 is rest, +x, +y, -x, -y, (++), (+-), (-+), (--);
+ *    D1Q3 is rest, +x, -x.
+ *  - Host pointers passed in are owned by the caller; the library copies from
+ *    or into them and never keeps them.  All device memory of a simulation
+ *    is owned by the library (or by the allocator the caller installs).
+ *  - Every call returns a status.  On failure, lbm_last_error() gives a
+ *    message for the calling thread.  No entry point faults or traps the
+ *    GPU on purpose: an unstable state (non-positive density or a non-finite
+ *    value) raises a device flag that lbm_sync, lbm_moments and
+ *    lbm_diagnostics report as LBM_EUNSTABLE.  A non-positive moment
+ *    temperature in thermal mode is not fatal (it makes b^eq more negative
+ *    and occurs transiently at sharp fronts); lbm_flags reports it.
+ *  - Thread safety: one simulation handle must not be used from two host
+ *    threads at once; different handles are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* invalid argument */
+    LBM_ENOMEM = 2,     /* device or host allocation failed, or over budget */
+    LBM_ECUDA = 3,      /* a CUDA runtime call failed */
+    LBM_EUNSTABLE = 4,  /* the state became non-physical (rho <= 0, NaN/Inf) */
+    LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LBM_EBUSY = 6,      /* result not ready yet (serving) */
+    LBM_EIO = 7         /* checkpoint file error */
+} lbm_status;
+
+typedef enum {
+    LBM_BC_PERIODIC = 0,    /* periodic on every axis */
+    LBM_BC_FIXED_STATE = 1  /* x: frozen equilibrium reservoirs carrying the
+                               initial state of the edge site of each row;
+                               y and z periodic */
+} lbm_bc;
+
+typedef enum {
+    LBM_F64 = 0,          /* populations and arithmetic in FP64 */
+    LBM_F32 = 1,          /* FP32 storage and arithmetic */
+    LBM_F16_SHIFTED = 2,  /* populations stored as FP16 deviations from the
+                             rest-state weight w_i; bbar in FP32; FP32 math */
+    LBM_BF16_SHIFTED = 3  /* as above with BF16 */
+} lbm_dtype;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory of at least `bytes` on the current device or NULL;
+ * free releases it. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct {
+    lbm_dtype dtype;        /* default LBM_F64 */
+    int thermal;            /* 0 (default): isothermal, T = T0 in b^eq, as in
+                               the paper's analysis (Sec. II.D, P = rho T);
+                               1: T from the trace of the full second moment,
+                               which conserves energy */
+    int device;             /* CUDA device ordinal, default 0 */
+    void *stream;           /* cudaStream_t to run on; NULL: the library
+                               creates its own non-blocking stream */
+    lbm_alloc_fn alloc;     /* NULL: cudaMalloc / cudaFree */
+    lbm_free_fn free;
+    void *alloc_ctx;
+    int tile;               /* kernel variant index; -1 (default): autotuned */
+    int chunk;              /* planes per block along the march axis; 0: auto */
+    int steps_per_launch;   /* small lattices: steps fused per launch; 0: auto */
+    int diagnostics;        /* 1 (default): every step also reduces mass,
+                               momentum and energy of the state it consumes
+                               into a device history (lbm_diagnostics_history);
+                               0: off */
+    int use_graphs;         /* 1 (default): lbm_step replays CUDA graphs */
+} lbm_opts;
+
+typedef struct lbm_sim lbm_sim;
+
+/* Fill *opts with the defaults listed above. */
+void lbm_default_opts(lbm_opts *opts);
+
+/* Create a simulation of a dim-dimensional lattice (dim 1: D1Q3, 2: D2Q9,
+ * 3: D3Q19; Sec. II.B) of nx*ny*nz sites (unused extents must be 1), with
+ * relaxation time tau > 0 (Eq. 55), reference temperature T0 > 0 and boundary
+ * bc.  Allocates the two emitted-state buffers (A-B ping-pong) on the device.
+ * The state is undefined until lbm_init.  *out receives the handle. */
+lbm_status lbm_create(int dim, int nx, int ny, int nz, double tau, double T0,
+                      lbm_bc bc, lbm_sim **out);
+lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
+                         lbm_bc bc, const lbm_opts *opts, lbm_sim **out);
+
+typedef struct {
+    const double *rho;  /* N values, > 0 */
+    const double *u;    /* dim planes of N values */
+    const double *T;    /* N values, > 0 */
+} lbm_fields_in;
+
+/* Set the state from host fields (rho, u, T): every site emits its local
+ * equilibrium fbar* = f^eq(rho, u) (Appendix A) and bbar* = b^eq(u, T)
+ * (Eq. 36); the state at t = 0 is what streams in.  For LBM_BC_FIXED_STATE the
+ * reservoirs take the state of the edge site of each row.  Resets the step
+ * counter.  Blocks until the copy is done. */
+lbm_status lbm_init(lbm_sim *sim, const lbm_fields_in *fields);
+
+/* Advance n >= 0 time steps (Sec. II.C, Eqs. 49-68): asynchronous on the
+ * simulation's stream. */
+lbm_status lbm_step(lbm_sim *sim, long n);
+
+/* Wait for the simulation's stream; reports LBM_EUNSTABLE if the device flag
+ * is set. */
+lbm_status lbm_sync(lbm_sim *sim);
+
+typedef struct {
+    double *rho;  /* N values or NULL */
+    double *u;    /* dim planes of N values or NULL: corrected velocity
+                     u = (sum fbar e + F/2)/rho (Eq. 57) */
+    double *T;    /* N values or NULL: moment temperature
+                     (E - rho|u|^2)/(dim rho), E = sum fbar|e|^2 + rho tr bbar
+                     + tr(G)/2 */
+} lbm_fields_out;
+
+/* Macroscopic fields of the current state, copied to the host.  Blocking. */
+lbm_status lbm_moments(lbm_sim *sim, lbm_fields_out *out);
+
+/* Global mass, momentum (dim values) and energy of the current state, summed
+ * in FP64: out[0] = sum rho, out[1..dim] = sum rho u, out[dim+1] = sum E.
+ * Blocking. */
+lbm_status lbm_diagnostics(lbm_sim *sim, double *out);
+
+/* The per-step diagnostics recorded by lbm_step when opts.diagnostics = 1:
+ * up to `cap` most recent records, oldest first, each dim+3 doubles
+ * (step index, mass, momentum..., energy).  *count receives the number
+ * written.  Blocking. */
+lbm_status lbm_diagnostics_history(lbm_sim *sim, double *out, int cap, int *count);
+
+/* The newest per-step record (step index, mass, momentum..., energy; dim+3
+ * doubles) written by lbm_step when opts.diagnostics = 1: a read of d+3
+ * doubles, the cheap per-step result.  Blocking.  LBM_EINVAL if no step has
+ * recorded diagnostics since lbm_init. */
+lbm_status lbm_last_diagnostics(lbm_sim *sim, double *out);
+
+/* Emitted (post-collision, about to stream) state in FP64 on the host:
+ * f: Q planes of N values (fbar*_i), b: nb planes of N values (bbar*).
+ * Either pointer may be NULL.  Blocking. */
+lbm_status lbm_get_state(lbm_sim *sim, double *f, double *b);
+
+/* Replace the emitted state from FP64 host planes (same layout), encoded to
+ * the storage dtype.  Reservoirs and the step counter are unchanged. */
+lbm_status lbm_set_state(lbm_sim *sim, const double *f, const double *b);
+
+/* Sticky status bits since lbm_init: bit 0 = a fatal state was seen (see
+ * LBM_EUNSTABLE), bit 1 = a non-positive moment temperature was seen
+ * (thermal mode).  Blocking. */
+lbm_status lbm_flags(lbm_sim *sim, int *flags);
+
+/* Number of steps taken since lbm_init. */
+long lbm_step_count(const lbm_sim *sim);
+
+/* Checkpoint: write / read the full state (emitted planes in the storage
+ * dtype, reservoirs, step counter, parameters) as a raw file with a small
+ * header.  lbm_load requires a simulation created with the same dim, extents,
+ * dtype and boundary.  A run of n steps equals n/2 steps + save + load + n/2
+ * steps bit for bit. */
+lbm_status lbm_save(lbm_sim *sim, const char *path);
+lbm_status lbm_load(lbm_sim *sim, const char *path);
+
+/* Free all device memory of the simulation. */
+void lbm_destroy(lbm_sim *sim);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *lbm_last_error(void);
+
+/* Library version string. */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -62,6 +62,7 @@ def lib():
         L.orc_diagnostics.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_emitted.argtypes = [ctypes.c_void_p, dp, dp]
         L.orc_get_state.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_set_emitted.argtypes = [ctypes.c_void_p, dp, dp]
         L.orc_gradient.argtypes = [ctypes.c_int] * 4 + [dp, dp]
         _lib = L
     return _lib
@@ -184,6 +185,12 @@ class Sim:
         b = np.zeros((self.nb,) + self.shape)
         lib().orc_get_emitted(self._h, _p(f), _p(b))
         return f, b
+
+    def set_emitted(self, f, b):
+        """Restart from an emitted state (Q, nz, ny, nx), (nb, nz, ny, nx)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        lib().orc_set_emitted(self._h, _p(f), _p(b))
 
     def state(self):
         """Pre-collision fbar and bbar at the current time."""

@@ -616,3 +616,21 @@ void orc_gradient(int d, int nx, int ny, int nz, const double *phi, double *out)
     }
     orc_destroy(s);
 }
+
+/* Replace the emitted state (Q planes, nb planes) and stream it, so that the
+ * state at the current time is what these emissions deliver (Eqs. 49, 66).
+ * Used to restart the oracle from a state produced elsewhere, e.g. a window
+ * cut out of a larger periodic lattice: after one step, sites at distance
+ * >= 2 from the window's edges are exact (the step reads the emitted state
+ * up to two sites away: one for the pull, one for the gradient).          */
+void orc_set_emitted(void *h, const double *f, const double *b)
+{
+    orc_sim *s = (orc_sim *)h;
+    int Q = s->L.Q, nb = s->L.nb;
+    long N = s->N;
+    for (long n = 0; n < N; ++n) {
+        for (int i = 0; i < Q; ++i) s->fs[n * Q + i] = f[i * N + n];
+        for (int k = 0; k < nb; ++k) s->bs[n * nb + k] = b[k * N + n];
+    }
+    phase_c(s);
+}

@@ -1,0 +1,731 @@
+// C-ABI runtime of the bump-function lattice Boltzmann library: simulation
+// objects, device buffers (A-B ping-pong of the emitted state), the tile /
+// chunk autotuner, CUDA-graph replay of step sequences, moments,
+// diagnostics and checkpoints.  See include/lbm.h for the contract.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+int q_of(int D) { return D == 3 ? 19 : (D == 2 ? 9 : 3); }
+int nb_of(int D) { return D == 3 ? 6 : (D == 2 ? 3 : 1); }
+size_t fbytes_of(int dtype) { return dtype == DT_F64 ? 8 : (dtype == DT_F32 ? 4 : 2); }
+size_t rbytes_of(int dtype) { return dtype == DT_F64 ? 8 : 4; }
+
+// autotune cache: (D, dtype, nx, ny, nz) -> (variant, chunk)
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;
+
+const int kHistCap = 4096;
+
+}  // namespace
+
+struct lbm_sim {
+    int D = 0, Q = 0, NB = 0;
+    int nx = 1, ny = 1, nz = 1;
+    long long N = 0, rows = 0;
+    double tau = 0, T0 = 0;
+    int bc = 0;
+    lbm_opts opts{};
+    int dtype = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* f[2] = {nullptr, nullptr};
+    void* b[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* gf = nullptr;
+    void* gb = nullptr;
+    void* gaux = nullptr;
+    double* partial = nullptr;
+    size_t partial_blocks = 0;
+    unsigned int* ticket = nullptr;
+    double* hist = nullptr;
+    long long* step_ctr = nullptr;
+    int* flag = nullptr;
+    double* diag_out = nullptr;
+    double* fields = nullptr;  // (D+2) N doubles: init input / moments output
+    int var = -1, chunk = 0;
+    long nstep = 0;
+    // graphs: [parity of cur] -> executable graph of kGraphSteps launches
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_steps = 0;
+    std::vector<std::pair<void*, size_t>> allocs;
+
+    void* dalloc(size_t bytes) {
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (opts.alloc) {
+            p = opts.alloc(bytes, opts.alloc_ctx);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) allocs.push_back({p, bytes});
+        return p;
+    }
+    void release() {
+        for (int k = 0; k < 2; ++k)
+            if (graph[k]) cudaGraphExecDestroy(graph[k]);
+        for (auto& a : allocs) {
+            if (opts.alloc && opts.free)
+                opts.free(a.first, a.second, opts.alloc_ctx);
+            else if (!opts.alloc)
+                cudaFree(a.first);
+        }
+        allocs.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+StepArgs base_args(const lbm_sim* s) {
+    StepArgs a{};
+    a.fin = s->f[s->cur];
+    a.bin = s->b[s->cur];
+    a.fout = s->f[1 - s->cur];
+    a.bout = s->b[1 - s->cur];
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.nz = s->nz;
+    a.chunk = s->chunk;
+    a.N = s->N;
+    a.omega = 1.0 / (s->tau + 0.5);
+    a.tau = s->tau;
+    a.T0 = s->T0;
+    a.thermal = s->opts.thermal;
+    a.fixed_x = s->bc == LBM_BC_FIXED_STATE;
+    a.rows = s->rows;
+    a.gf = s->gf;
+    a.gb = s->gb;
+    a.gaux = s->gaux;
+    a.partial = s->partial;
+    a.ticket = s->ticket;
+    a.step_ctr = s->step_ctr;
+    a.flag = s->flag;
+    a.hist_cap = kHistCap;
+    return a;
+}
+
+size_t blocks_of(const lbm_sim* s, int v, int chunk) {
+    dim3 g = step_grid(s->D, v, s->nx, s->ny, s->nz, chunk);
+    return (size_t)g.x * g.y * g.z;
+}
+
+// Chunk candidates along the march axis: keep at least ~4 waves of blocks on
+// 152 SMs while amortising the two-plane ring of each chunk.
+std::vector<int> chunk_candidates(const lbm_sim* s) {
+    int np = s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1);
+    if (s->D == 1) return {1};
+    std::vector<int> c;
+    for (int k : {8, 16, 32, 64, 128, 256}) {
+        if (k >= np) {
+            c.push_back(np);
+            break;
+        }
+        c.push_back(k);
+    }
+    return c;
+}
+
+lbm_status ensure_partial(lbm_sim* s, int v, int chunk) {
+    size_t nb = blocks_of(s, v, chunk);
+    if (nb <= s->partial_blocks) return LBM_OK;
+    double* p = (double*)s->dalloc(nb * (s->D + 2) * sizeof(double));
+    if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");
+    s->partial = p;
+    s->partial_blocks = nb;
+    return LBM_OK;
+}
+
+lbm_status launch_one_step(lbm_sim* s, bool diag) {
+    StepArgs a = base_args(s);
+    a.write_state = 1;
+    a.want_diag = diag ? 1 : 0;
+    a.hist = s->hist;
+    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    s->cur = 1 - s->cur;
+    return LBM_OK;
+}
+
+lbm_status autotune(lbm_sim* s) {
+    auto key = std::make_tuple(s->D, s->dtype, s->nx, s->ny, s->nz);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            s->var = it->second.first;
+            s->chunk = it->second.second;
+            return ensure_partial(s, s->var, s->chunk);
+        }
+    }
+    int nv = n_variants(s->D);
+    std::vector<int> vars;
+    if (s->opts.tile >= 0 && s->opts.tile < nv)
+        vars.push_back(s->opts.tile);
+    else
+        for (int v = 0; v < nv; ++v) vars.push_back(v);
+    std::vector<int> chunks = s->opts.chunk > 0 ? std::vector<int>{s->opts.chunk} : chunk_candidates(s);
+    if (vars.size() * chunks.size() == 1) {
+        s->var = vars[0];
+        s->chunk = chunks[0];
+        return ensure_partial(s, s->var, s->chunk);
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bv = vars[0], bc = chunks[0];
+    // Candidates read the current state and write the other buffer only, so
+    // the simulation state is untouched; no diagnostics, no flag updates
+    // beyond what a real step would raise.
+    for (int v : vars) {
+        for (int c : chunks) {
+            StepArgs a = base_args(s);
+            a.chunk = c;
+            a.write_state = 1;
+            a.want_diag = 0;
+            size_t smem = step_smem(s->D, s->dtype, v);
+            if (smem > 227 * 1024) continue;
+            cudaError_t e = launch_step(s->D, s->dtype, v, a, s->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            const int reps = 3;
+            CK(cudaEventRecord(e0, s->stream));
+            for (int r = 0; r < reps; ++r) CK(launch_step(s->D, s->dtype, v, a, s->stream));
+            CK(cudaEventRecord(e1, s->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bv = v;
+                bc = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->var = bv;
+    s->chunk = bc;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[key] = {bv, bc};
+    }
+    return ensure_partial(s, s->var, s->chunk);
+}
+
+lbm_status ensure_tuned(lbm_sim* s) {
+    if (s->var >= 0) return LBM_OK;
+    return autotune(s);
+}
+
+lbm_status build_graph(lbm_sim* s, int parity, int steps) {
+    cudaGraph_t g;
+    int saved = s->cur;
+    s->cur = parity;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < steps && st == LBM_OK; ++k) st = launch_one_step(s, s->opts.diagnostics != 0);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    s->cur = saved;
+    if (st != LBM_OK) return st;
+    CK(e);
+    e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LBM_OK;
+}
+
+lbm_status check_flag(lbm_sim* s) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (h & 1) return fail(LBM_EUNSTABLE, "state became non-physical (rho <= 0 or not finite)");
+    return LBM_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->dtype = LBM_F64;
+    o->thermal = 0;
+    o->device = 0;
+    o->stream = nullptr;
+    o->tile = -1;
+    o->chunk = 0;
+    o->steps_per_launch = 0;
+    o->diagnostics = 1;
+    o->use_graphs = 1;
+}
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+const char* lbm_version(void) { return "bump-lbm-gb300 0.1 (sm_103a)"; }
+
+lbm_status lbm_create(int dim, int nx, int ny, int nz, double tau, double T0, lbm_bc bc, lbm_sim** out) {
+    lbm_opts o;
+    lbm_default_opts(&o);
+    return lbm_create_ex(dim, nx, ny, nz, tau, T0, bc, &o, out);
+}
+
+lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0, lbm_bc bc, const lbm_opts* opts,
+                         lbm_sim** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dim < 1 || dim > 3) return fail(LBM_EINVAL, "dim must be 1, 2 or 3");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
+    if ((dim < 2 && ny != 1) || (dim < 3 && nz != 1)) return fail(LBM_EINVAL, "unused extents must be 1");
+    if (!(tau > 0) || !(T0 > 0)) return fail(LBM_EINVAL, "tau and T0 must be > 0");
+    if (bc != LBM_BC_PERIODIC && bc != LBM_BC_FIXED_STATE) return fail(LBM_EINVAL, "unknown boundary");
+    lbm_opts o;
+    if (opts)
+        o = *opts;
+    else
+        lbm_default_opts(&o);
+    if (o.dtype < LBM_F64 || o.dtype > LBM_BF16_SHIFTED) return fail(LBM_EINVAL, "unknown dtype");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(LBM_EINVAL, "alloc and free go together");
+    long long N = (long long)nx * ny * nz;
+    int Q = q_of(dim), NB = nb_of(dim);
+    if ((long long)Q * N >= (1LL << 40)) return fail(LBM_EINVAL, "lattice too large");
+
+    lbm_sim* s = new lbm_sim();
+    s->D = dim;
+    s->Q = Q;
+    s->NB = NB;
+    s->nx = nx;
+    s->ny = ny;
+    s->nz = nz;
+    s->N = N;
+    s->rows = (long long)ny * nz;
+    s->tau = tau;
+    s->T0 = T0;
+    s->bc = bc;
+    s->opts = o;
+    s->dtype = (int)o.dtype;
+    s->device = o.device;
+    DeviceGuard dg(s->device);
+    cudaError_t e;
+    if (o.stream) {
+        s->stream = (cudaStream_t)o.stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return fail(LBM_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+        }
+        s->own_stream = true;
+    }
+    size_t fb = fbytes_of(s->dtype), rb = rbytes_of(s->dtype);
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        s->f[k] = s->dalloc((size_t)Q * N * fb);
+        s->b[k] = s->dalloc((size_t)NB * N * rb);
+        ok = s->f[k] && s->b[k];
+    }
+    if (ok && bc == LBM_BC_FIXED_STATE) {
+        s->gf = s->dalloc((size_t)2 * Q * s->rows * rb);
+        s->gb = s->dalloc((size_t)2 * NB * s->rows * rb);
+        s->gaux = s->dalloc((size_t)2 * (dim + NB) * s->rows * rb);
+        ok = s->gf && s->gb && s->gaux;
+    }
+    if (ok) {
+        s->ticket = (unsigned int*)s->dalloc(64);
+        s->step_ctr = (long long*)s->dalloc(64);
+        s->flag = (int*)s->dalloc(64);
+        s->diag_out = (double*)s->dalloc(64);
+        s->hist = (double*)s->dalloc((size_t)kHistCap * (dim + 3) * sizeof(double));
+        ok = s->ticket && s->step_ctr && s->flag && s->diag_out && s->hist;
+    }
+    if (!ok) {
+        s->release();
+        delete s;
+        return fail(LBM_ENOMEM, "device allocation failed");
+    }
+    cudaMemsetAsync(s->ticket, 0, 64, s->stream);
+    cudaMemsetAsync(s->step_ctr, 0, 64, s->stream);
+    cudaMemsetAsync(s->flag, 0, 64, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        s->release();
+        delete s;
+        return fail(LBM_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_sim* s) {
+    if (!s) return;
+    DeviceGuard dg(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    s->release();
+    delete s;
+}
+
+static lbm_status ensure_fields(lbm_sim* s) {
+    if (s->fields) return LBM_OK;
+    s->fields = (double*)s->dalloc((size_t)(s->D + 2) * s->N * sizeof(double));
+    if (!s->fields) return fail(LBM_ENOMEM, "fields buffer");
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
+    if (!s || !in || !in->rho || !in->u || !in->T) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    const long long N = s->N;
+    for (long long k = 0; k < N; ++k)
+        if (!(in->rho[k] > 0) || !(in->T[k] > 0)) return fail(LBM_EINVAL, "rho and T must be positive");
+    lbm_status st = ensure_fields(s);
+    if (st != LBM_OK) return st;
+    double* rho = s->fields;
+    double* u = rho + N;
+    double* T = u + (size_t)s->D * N;
+    CK(cudaMemcpyAsync(rho, in->rho, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(u, in->u, (size_t)s->D * N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(T, in->T, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    s->cur = 0;
+    CK(launch_init(s->D, s->dtype, rho, u, T, s->f[0], s->b[0], N, s->stream));
+    if (s->bc == LBM_BC_FIXED_STATE)
+        CK(launch_reservoir(s->D, s->dtype, rho, u, T, s->nx, s->rows, N, s->gf, s->gb, s->gaux, s->stream));
+    CK(cudaMemsetAsync(s->step_ctr, 0, 64, s->stream));
+    CK(cudaMemsetAsync(s->flag, 0, 64, s->stream));
+    CK(cudaMemsetAsync(s->ticket, 0, 64, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->nstep = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_sim* s, long n) {
+    if (!s) return fail(LBM_EINVAL, "NULL sim");
+    if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    DeviceGuard dg(s->device);
+    lbm_status st = ensure_tuned(s);
+    if (st != LBM_OK) return st;
+    const bool diag = s->opts.diagnostics != 0;
+    const int K = s->graph_steps;
+    long done = 0;
+    if (s->opts.use_graphs && s->stream != nullptr && n >= 2) {
+        if (K == 0) {
+            // graph length: more launches per replay for small lattices
+            int steps = (s->N * s->Q < (1LL << 22)) ? 32 : 2;
+            s->graph_steps = steps;
+        }
+        const int GK = s->graph_steps;
+        while (n - done >= GK) {
+            if (!s->graph[s->cur]) {
+                st = build_graph(s, s->cur, GK);
+                if (st != LBM_OK) return st;
+            }
+            CK(cudaGraphLaunch(s->graph[s->cur], s->stream));
+            if (GK % 2) s->cur = 1 - s->cur;
+            done += GK;
+        }
+    }
+    for (; done < n; ++done) {
+        st = launch_one_step(s, diag);
+        if (st != LBM_OK) return st;
+    }
+    s->nstep += n;
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_sim* s) {
+    if (!s) return fail(LBM_EINVAL, "NULL sim");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    return check_flag(s);
+}
+
+long lbm_step_count(const lbm_sim* s) { return s ? s->nstep : -1; }
+
+lbm_status lbm_flags(lbm_sim* s, int* flags) {
+    if (!s || !flags) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    CK(cudaMemcpyAsync(flags, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_sim* s, lbm_fields_out* out) {
+    if (!s || !out) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    lbm_status st = ensure_tuned(s);
+    if (st != LBM_OK) return st;
+    st = ensure_fields(s);
+    if (st != LBM_OK) return st;
+    StepArgs a = base_args(s);
+    a.write_state = 0;
+    a.want_diag = 0;
+    a.mout = s->fields;
+    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    const long long N = s->N;
+    if (out->rho) CK(cudaMemcpyAsync(out->rho, s->fields, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (out->u)
+        CK(cudaMemcpyAsync(out->u, s->fields + N, (size_t)s->D * N * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->stream));
+    if (out->T)
+        CK(cudaMemcpyAsync(out->T, s->fields + (size_t)(1 + s->D) * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_flag(s);
+}
+
+lbm_status lbm_diagnostics(lbm_sim* s, double* out) {
+    if (!s || !out) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    lbm_status st = ensure_tuned(s);
+    if (st != LBM_OK) return st;
+    StepArgs a = base_args(s);
+    a.write_state = 0;
+    a.want_diag = 1;
+    a.diag_out = s->diag_out;
+    a.hist = nullptr;
+    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    CK(cudaMemcpyAsync(out, s->diag_out, (size_t)(s->D + 2) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_flag(s);
+}
+
+lbm_status lbm_diagnostics_history(lbm_sim* s, double* out, int cap, int* count) {
+    if (!s || !out || !count || cap < 0) return fail(LBM_EINVAL, "bad argument");
+    DeviceGuard dg(s->device);
+    long long ctr = 0;
+    CK(cudaMemcpyAsync(&ctr, s->step_ctr, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const int rec = s->D + 3;
+    long long avail = ctr < kHistCap ? ctr : kHistCap;
+    long long n = avail < cap ? avail : cap;
+    std::vector<double> h((size_t)kHistCap * rec);
+    CK(cudaMemcpy(h.data(), s->hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < n; ++k) {
+        long long idx = (ctr - n + k) % kHistCap;
+        std::memcpy(out + k * rec, h.data() + idx * rec, rec * sizeof(double));
+    }
+    *count = (int)n;
+    return LBM_OK;
+}
+
+lbm_status lbm_last_diagnostics(lbm_sim* s, double* out) {
+    if (!s || !out) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    long long ctr = 0;
+    CK(cudaMemcpyAsync(&ctr, s->step_ctr, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (ctr <= 0) return fail(LBM_EINVAL, "no diagnostics recorded yet");
+    const int rec = s->D + 3;
+    CK(cudaMemcpyAsync(out, s->hist + ((ctr - 1) % kHistCap) * rec, rec * sizeof(double), cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_flag(s);
+}
+
+lbm_status lbm_get_state(lbm_sim* s, double* f, double* b) {
+    if (!s) return fail(LBM_EINVAL, "NULL sim");
+    DeviceGuard dg(s->device);
+    const long long N = s->N;
+    double* tmp = (double*)s->dalloc((size_t)(s->Q + s->NB) * N * sizeof(double));
+    if (!tmp) return fail(LBM_ENOMEM, "state staging buffer");
+    lbm_status st = LBM_OK;
+    cudaError_t e = launch_get_state(s->D, s->dtype, s->f[s->cur], s->b[s->cur], tmp, tmp + (size_t)s->Q * N, N,
+                                     s->stream);
+    if (e == cudaSuccess && f)
+        e = cudaMemcpyAsync(f, tmp, (size_t)s->Q * N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && b)
+        e = cudaMemcpyAsync(b, tmp + (size_t)s->Q * N, (size_t)s->NB * N * sizeof(double), cudaMemcpyDeviceToHost,
+                            s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = fail(LBM_ECUDA, std::string("get_state: ") + cudaGetErrorString(e));
+    // release the staging buffer
+    for (size_t k = 0; k < s->allocs.size(); ++k)
+        if (s->allocs[k].first == tmp) {
+            if (s->opts.alloc)
+                s->opts.free(tmp, s->allocs[k].second, s->opts.alloc_ctx);
+            else
+                cudaFree(tmp);
+            s->allocs.erase(s->allocs.begin() + k);
+            break;
+        }
+    return st;
+}
+
+lbm_status lbm_set_state(lbm_sim* s, const double* f, const double* b) {
+    if (!s) return fail(LBM_EINVAL, "NULL sim");
+    DeviceGuard dg(s->device);
+    const long long N = s->N;
+    double* tmp = (double*)s->dalloc((size_t)(s->Q + s->NB) * N * sizeof(double));
+    if (!tmp) return fail(LBM_ENOMEM, "state staging buffer");
+    cudaError_t e = cudaSuccess;
+    if (f) e = cudaMemcpyAsync(tmp, f, (size_t)s->Q * N * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && b)
+        e = cudaMemcpyAsync(tmp + (size_t)s->Q * N, b, (size_t)s->NB * N * sizeof(double), cudaMemcpyHostToDevice,
+                            s->stream);
+    if (e == cudaSuccess)
+        e = launch_set_state(s->D, s->dtype, s->f[s->cur], s->b[s->cur], f ? tmp : nullptr,
+                             b ? tmp + (size_t)s->Q * N : nullptr, N, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    lbm_status st = e == cudaSuccess ? LBM_OK : fail(LBM_ECUDA, std::string("set_state: ") + cudaGetErrorString(e));
+    for (size_t k = 0; k < s->allocs.size(); ++k)
+        if (s->allocs[k].first == tmp) {
+            if (s->opts.alloc)
+                s->opts.free(tmp, s->allocs[k].second, s->opts.alloc_ctx);
+            else
+                cudaFree(tmp);
+            s->allocs.erase(s->allocs.begin() + k);
+            break;
+        }
+    return st;
+}
+
+// Checkpoint file: header, then the emitted planes in the storage dtype, then
+// the reservoirs (fixed-state boundary only).
+struct CkptHeader {
+    char magic[8];
+    int D, nx, ny, nz, dtype, bc, thermal, pad;
+    double tau, T0;
+    long long nstep;
+};
+
+lbm_status lbm_save(lbm_sim* s, const char* path) {
+    if (!s || !path) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    const long long N = s->N;
+    size_t fb = (size_t)s->Q * N * fbytes_of(s->dtype), bb = (size_t)s->NB * N * rbytes_of(s->dtype);
+    std::vector<char> buf(fb + bb);
+    CK(cudaMemcpy(buf.data(), s->f[s->cur], fb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data() + fb, s->b[s->cur], bb, cudaMemcpyDeviceToHost));
+    size_t rb = rbytes_of(s->dtype);
+    size_t g1 = 0, g2 = 0, g3 = 0;
+    std::vector<char> gbuf;
+    if (s->bc == LBM_BC_FIXED_STATE) {
+        g1 = (size_t)2 * s->Q * s->rows * rb;
+        g2 = (size_t)2 * s->NB * s->rows * rb;
+        g3 = (size_t)2 * (s->D + s->NB) * s->rows * rb;
+        gbuf.resize(g1 + g2 + g3);
+        CK(cudaMemcpy(gbuf.data(), s->gf, g1, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(gbuf.data() + g1, s->gb, g2, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(gbuf.data() + g1 + g2, s->gaux, g3, cudaMemcpyDeviceToHost));
+    }
+    CkptHeader h{};
+    std::memcpy(h.magic, "BUMPLBM1", 8);
+    h.D = s->D;
+    h.nx = s->nx;
+    h.ny = s->ny;
+    h.nz = s->nz;
+    h.dtype = s->dtype;
+    h.bc = s->bc;
+    h.thermal = s->opts.thermal;
+    h.tau = s->tau;
+    h.T0 = s->T0;
+    h.nstep = s->nstep;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(LBM_EIO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size() &&
+              (gbuf.empty() || std::fwrite(gbuf.data(), 1, gbuf.size(), fp) == gbuf.size());
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(LBM_EIO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_sim* s, const char* path) {
+    if (!s || !path) return fail(LBM_EINVAL, "NULL argument");
+    DeviceGuard dg(s->device);
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(LBM_EIO, std::string("cannot open ") + path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "BUMPLBM1", 8) != 0) {
+        std::fclose(fp);
+        return fail(LBM_EIO, "not a checkpoint file");
+    }
+    if (h.D != s->D || h.nx != s->nx || h.ny != s->ny || h.nz != s->nz || h.dtype != s->dtype || h.bc != s->bc) {
+        std::fclose(fp);
+        return fail(LBM_EINVAL, "checkpoint does not match this simulation");
+    }
+    const long long N = s->N;
+    size_t fb = (size_t)s->Q * N * fbytes_of(s->dtype), bb = (size_t)s->NB * N * rbytes_of(s->dtype);
+    std::vector<char> buf(fb + bb);
+    bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    size_t rb = rbytes_of(s->dtype);
+    std::vector<char> gbuf;
+    size_t g1 = 0, g2 = 0, g3 = 0;
+    if (ok && s->bc == LBM_BC_FIXED_STATE) {
+        g1 = (size_t)2 * s->Q * s->rows * rb;
+        g2 = (size_t)2 * s->NB * s->rows * rb;
+        g3 = (size_t)2 * (s->D + s->NB) * s->rows * rb;
+        gbuf.resize(g1 + g2 + g3);
+        ok = std::fread(gbuf.data(), 1, gbuf.size(), fp) == gbuf.size();
+    }
+    std::fclose(fp);
+    if (!ok) return fail(LBM_EIO, "truncated checkpoint");
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(s->f[s->cur], buf.data(), fb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->b[s->cur], buf.data() + fb, bb, cudaMemcpyHostToDevice));
+    if (!gbuf.empty()) {
+        CK(cudaMemcpy(s->gf, gbuf.data(), g1, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->gb, gbuf.data() + g1, g2, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->gaux, gbuf.data() + g1 + g2, g3, cudaMemcpyHostToDevice));
+    }
+    s->opts.thermal = h.thermal;
+    s->tau = h.tau;
+    s->T0 = h.T0;
+    s->nstep = (long)h.nstep;
+    long long ctr = h.nstep;
+    CK(cudaMemcpy(s->step_ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->flag, 0, sizeof(int)));
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    return LBM_OK;
+}
+
+}  // extern "C"

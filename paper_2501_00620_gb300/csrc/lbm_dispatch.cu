@@ -1,0 +1,83 @@
+// Dimension dispatch for the kernel launchers.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+#define LBM_DECLARE_D(DD)                                                                                       \
+    cudaError_t launch_step_d##DD(int dtype, int v, const StepArgs& a, cudaStream_t st);                         \
+    size_t step_smem_d##DD(int dtype, int v);                                                                    \
+    int n_variants_d##DD();                                                                                      \
+    Variant variant_d##DD(int v);                                                                                \
+    cudaError_t launch_init_d##DD(int dtype, const double* rho, const double* u, const double* T, void* f,       \
+                                 void* b, long long N, cudaStream_t st);                                        \
+    cudaError_t launch_reservoir_d##DD(int dtype, const double* rho, const double* u, const double* T, int nx,   \
+                                      long long rows, long long N, void* gf, void* gb, void* gaux,              \
+                                      cudaStream_t st);                                                         \
+    cudaError_t launch_get_state_d##DD(int dtype, const void* f, const void* b, double* fo, double* bo,          \
+                                      long long N, cudaStream_t st);                                            \
+    cudaError_t launch_set_state_d##DD(int dtype, void* f, void* b, const double* fi, const double* bi,          \
+                                      long long N, cudaStream_t st);
+LBM_DECLARE_D(1)
+LBM_DECLARE_D(2)
+LBM_DECLARE_D(3)
+#undef LBM_DECLARE_D
+
+#define LBM_BY_D(D, call1, call2, call3, bad) \
+    ((D) == 1 ? (call1) : (D) == 2 ? (call2) : (D) == 3 ? (call3) : (bad))
+
+int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
+
+Variant variant(int D, int v) {
+    return LBM_BY_D(D, variant_d1(v), variant_d2(v), variant_d3(v), (Variant{0, 0}));
+}
+
+size_t step_smem(int D, int dtype, int v) {
+    return LBM_BY_D(D, step_smem_d1(dtype, v), step_smem_d2(dtype, v), step_smem_d3(dtype, v), (size_t)0);
+}
+
+dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk) {
+    Variant t = v >= 0 ? variant(D, v) : Variant{1, 1};
+    dim3 g(1, 1, 1);
+    g.x = (nx + t.tx - 1) / t.tx;
+    if (D == 3) {
+        g.y = (ny + t.ty - 1) / t.ty;
+        g.z = (nz + chunk - 1) / chunk;
+    } else if (D == 2) {
+        g.z = (ny + chunk - 1) / chunk;
+    }
+    return g;
+}
+
+cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t st) {
+    return LBM_BY_D(D, launch_step_d1(dtype, v, a, st), launch_step_d2(dtype, v, a, st),
+                    launch_step_d3(dtype, v, a, st), cudaErrorInvalidValue);
+}
+
+cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f, void* b,
+                        long long N, cudaStream_t st) {
+    return LBM_BY_D(D, launch_init_d1(dtype, rho, u, T, f, b, N, st), launch_init_d2(dtype, rho, u, T, f, b, N, st),
+                    launch_init_d3(dtype, rho, u, T, f, b, N, st), cudaErrorInvalidValue);
+}
+
+cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,
+                             long long rows, long long N, void* gf, void* gb, void* gaux, cudaStream_t st) {
+    return LBM_BY_D(D, launch_reservoir_d1(dtype, rho, u, T, nx, rows, N, gf, gb, gaux, st),
+                    launch_reservoir_d2(dtype, rho, u, T, nx, rows, N, gf, gb, gaux, st),
+                    launch_reservoir_d3(dtype, rho, u, T, nx, rows, N, gf, gb, gaux, st), cudaErrorInvalidValue);
+}
+
+cudaError_t launch_get_state(int D, int dtype, const void* f, const void* b, double* fo, double* bo, long long N,
+                             cudaStream_t st) {
+    return LBM_BY_D(D, launch_get_state_d1(dtype, f, b, fo, bo, N, st),
+                    launch_get_state_d2(dtype, f, b, fo, bo, N, st),
+                    launch_get_state_d3(dtype, f, b, fo, bo, N, st), cudaErrorInvalidValue);
+}
+
+cudaError_t launch_set_state(int D, int dtype, void* f, void* b, const double* fi, const double* bi, long long N,
+                             cudaStream_t st) {
+    return LBM_BY_D(D, launch_set_state_d1(dtype, f, b, fi, bi, N, st),
+                    launch_set_state_d2(dtype, f, b, fi, bi, N, st),
+                    launch_set_state_d3(dtype, f, b, fi, bi, N, st), cudaErrorInvalidValue);
+}
+
+}  // namespace lbm

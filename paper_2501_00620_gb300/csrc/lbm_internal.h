@@ -1,0 +1,35 @@
+// Internal interface between the C-ABI runtime and the per-dimension kernel
+// launchers.  Not part of the public header.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+enum Dtype { DT_F64 = 0, DT_F32 = 1, DT_F16 = 2, DT_BF16 = 3 };
+
+struct Variant {
+    int tx, ty;
+};
+
+// Kernel variants (tile shapes) available for a dimension.
+int n_variants(int D);
+Variant variant(int D, int v);
+size_t step_smem(int D, int dtype, int v);
+
+// Grid of a step launch for extents and chunk.
+dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk);
+
+cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
+                        void* b, long long N, cudaStream_t st);
+cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,
+                             long long rows, long long N, void* gf, void* gb, void* gaux, cudaStream_t st);
+cudaError_t launch_get_state(int D, int dtype, const void* f, const void* b, double* fo, double* bo,
+                             long long N, cudaStream_t st);
+cudaError_t launch_set_state(int D, int dtype, void* f, void* b, const double* fi, const double* bi,
+                             long long N, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,121 @@
+// Launchers for the D3 lattice (tile variants x storage types).
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+constexpr int kD = 3;
+constexpr Variant kVariants[] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}};
+constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
+
+template <typename FS, int TX, int TY>
+cudaError_t launch_one(const StepArgs& a, cudaStream_t st) {
+    using Sh = StepShape<kD, FS, TX, TY>;
+    auto kern = step_kernel<kD, FS, TX, TY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid = step_grid(kD, -1, a.nx, a.ny, a.nz, a.chunk);
+    grid.x = (a.nx + TX - 1) / TX;
+    if (kD == 3) grid.y = (a.ny + TY - 1) / TY;
+    kern<<<grid, TX * TY, Sh::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename FS>
+cudaError_t launch_dtype(int v, const StepArgs& a, cudaStream_t st) {
+    switch (v) {
+        case 0: return launch_one<FS, 32, 8>(a, st);
+        case 1: return launch_one<FS, 32, 4>(a, st);
+        case 2: return launch_one<FS, 64, 4>(a, st);
+        case 3: return launch_one<FS, 32, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename FS>
+size_t smem_of(int v) {
+    switch (v) {
+        case 0: return StepShape<kD, FS, 32, 8>::smem;
+        case 1: return StepShape<kD, FS, 32, 4>::smem;
+        case 2: return StepShape<kD, FS, 64, 4>::smem;
+        case 3: return StepShape<kD, FS, 32, 16>::smem;
+        default: return 0;
+    }
+}
+
+template <typename F>
+cudaError_t by_dtype(int dtype, F&& f) {
+    switch (dtype) {
+        case DT_F64: return f(double{});
+        case DT_F32: return f(float{});
+        case DT_F16: return f(__half{});
+        case DT_BF16: return f(__nv_bfloat16{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+}  // namespace
+
+cudaError_t launch_step_d3(int dtype, int v, const StepArgs& a, cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) { return launch_dtype<decltype(tag)>(v, a, st); });
+}
+
+size_t step_smem_d3(int dtype, int v) {
+    switch (dtype) {
+        case DT_F64: return smem_of<double>(v);
+        case DT_F32: return smem_of<float>(v);
+        case DT_F16: return smem_of<__half>(v);
+        case DT_BF16: return smem_of<__nv_bfloat16>(v);
+    }
+    return 0;
+}
+
+int n_variants_d3() { return kNV; }
+Variant variant_d3(int v) { return kVariants[v]; }
+
+cudaError_t launch_init_d3(int dtype, const double* rho, const double* u, const double* T, void* f, void* b,
+                            long long N, cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) {
+        using FS = decltype(tag);
+        init_kernel<kD, FS><<<blocks_for(N, 256), 256, 0, st>>>(
+            rho, u, T, static_cast<FS*>(f), static_cast<typename Store<FS>::breal*>(b), N);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_reservoir_d3(int dtype, const double* rho, const double* u, const double* T, int nx,
+                                 long long rows, long long N, void* gf, void* gb, void* gaux, cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) {
+        using R = typename Store<decltype(tag)>::real;
+        reservoir_kernel<kD, R><<<blocks_for(2 * rows, 256), 256, 0, st>>>(
+            rho, u, T, nx, rows, N, static_cast<R*>(gf), static_cast<R*>(gb), static_cast<R*>(gaux));
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_get_state_d3(int dtype, const void* f, const void* b, double* fo, double* bo, long long N,
+                                 cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) {
+        using FS = decltype(tag);
+        get_state_kernel<kD, FS><<<blocks_for(N, 256), 256, 0, st>>>(
+            static_cast<const FS*>(f), static_cast<const typename Store<FS>::breal*>(b), fo, bo, N);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_set_state_d3(int dtype, void* f, void* b, const double* fi, const double* bi, long long N,
+                                 cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) {
+        using FS = decltype(tag);
+        set_state_kernel<kD, FS><<<blocks_for(N, 256), 256, 0, st>>>(
+            static_cast<FS*>(f), static_cast<typename Store<FS>::breal*>(b), fi, bi, N);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace lbm

@@ -1,0 +1,540 @@
+// Fused single-pass update of the bump-function lattice Boltzmann method
+// (arXiv 2501.00620, Sec. II.C), pull scheme with A-B buffers.
+//
+// Stored state: the EMITTED (post-collision, about-to-stream) populations
+// S_i(x) = fbar*_i(x) and variance bt*(x) of the last step.  One launch maps
+// S(t) -> S(t+1):
+//   stage 1 (every site of the tile plus a one-site ring):
+//     pull fbar_i(x) = S_i(x - e_i) (Eq. 49) and the mass-weighted variance
+//     bbar(x) = sum_i fbar_i bt*(x - e_i) / rho (Eq. 66); moments rho, j0,
+//     Ebar (Eqs. 56-57 before correction); rho*b for the gradient with b^eq at
+//     the uncorrected velocity (Eq. 68); u0 and rho*b go to shared memory.
+//   stage 2 (tile sites):
+//     F = -div(rho b) (Eq. 59), G = -div(rho u0 b + rho u0 b) (Eq. 61) by the
+//     lattice-weight central difference d_a phi = 3 sum_i w_i e_ia phi(x+e_i);
+//     u = (j0 + F/2)/rho (Eq. 57); T (isothermal T0 or thermal);
+//     fbar* = fbar + omega (f^eq + tau Phi - fbar) (Eq. 55);
+//     bbar* = bbar + omega (b^eq - bbar) (Eqs. 63, 65); store S(t+1).
+// The gradient needs rho*b on the neighbours, which exist only after the
+// neighbours have pulled; the ring is recomputed per tile (stage 1 on
+// (TX+2) x (TY+2) sites per plane) and the kernel marches along the slowest
+// axis keeping three planes of (u0, rho b) in a rolling shared-memory window,
+// so each stored value is read from HBM about once per step.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+struct StepArgs {
+    const void* fin;      // Q planes, storage type: emitted df at t
+    const void* bin;      // NB planes, breal: emitted bt at t
+    void* fout;           // Q planes: emitted df at t+1 (write_state)
+    void* bout;           // NB planes
+    int nx, ny, nz;
+    int chunk;            // planes per block along the march axis
+    long long N;
+    double omega, tau, T0;
+    int thermal;
+    int fixed_x;          // 1: frozen reservoirs outside [0, nx)
+    long long rows;       // ny * nz (reservoir rows)
+    const void* gf;       // reservoirs, real: [2][Q][rows] df
+    const void* gb;       // [2][NB][rows] bt
+    const void* gaux;     // [2][D+NB][rows] u (D), rho*b (NB)
+    int write_state;      // 1: collide and store S(t+1)
+    double* mout;         // if non-null: rho (N), u (D*N), T (N) in FP64
+    int want_diag;        // 1: reduce mass, momentum, energy of the state at t
+    double* partial;      // [gridDim total][D+2] per-block sums
+    unsigned int* ticket; // completion counter for the last-block reduction
+    double* diag_out;     // if non-null: the D+2 global sums
+    double* hist;         // history ring: records of D+3 doubles
+    int hist_cap;
+    long long* step_ctr;  // device step counter (history index)
+    int* flag;            // bit 0: fatal (rho <= 0 or non-finite); bit 1: T <= 0 seen
+};
+
+__device__ __forceinline__ int wrap1(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+__device__ __forceinline__ int modp(int c, int n) {
+    int r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+
+// Shared-memory footprint of the aux window: 3 planes x (D + NB) x region.
+template <int D, typename FS, int TX, int TY> struct StepShape {
+    using L = Lattice<D>;
+    using real = typename Store<FS>::real;
+    static constexpr int RX = TX + 2;
+    static constexpr int RY = (D == 3) ? TY + 2 : 1;
+    static constexpr int RS = RX * RY;
+    static constexpr int NAUX = D + L::NB;
+    static constexpr int NSLOT = (D == 1) ? 1 : 3;
+    static constexpr size_t aux_bytes = (sizeof(real) * NSLOT * NAUX * RS + 15) / 16 * 16;
+    static constexpr size_t smem = aux_bytes + sizeof(double) * 32 * (D + 2);
+};
+
+template <int D, typename FS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
+    using L = Lattice<D>;
+    using Sh = StepShape<D, FS, TX, TY>;
+    using real = typename Store<FS>::real;
+    using breal = typename Store<FS>::breal;
+    constexpr int Q = L::Q, NB = L::NB, NAUX = Sh::NAUX;
+    constexpr int RX = Sh::RX, RS = Sh::RS, NSLOT = Sh::NSLOT;
+    constexpr int NT = TX * TY;
+    constexpr int NRING = RS - TX * TY;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* aux = reinterpret_cast<real*>(smem_raw);  // [NSLOT][NAUX][RS]
+    double* red = reinterpret_cast<double*>(smem_raw + Sh::aux_bytes);
+
+    const FS* __restrict__ fin = static_cast<const FS*>(a.fin);
+    const breal* __restrict__ bin = static_cast<const breal*>(a.bin);
+    const real* __restrict__ gf = static_cast<const real*>(a.gf);
+    const real* __restrict__ gb = static_cast<const real*>(a.gb);
+    const real* __restrict__ gaux = static_cast<const real*>(a.gaux);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = (D == 3) ? blockIdx.y * TY : 0;
+    const int np = (D == 3) ? a.nz : (D == 2 ? a.ny : 1);
+    const int p0 = (D == 1) ? 0 : blockIdx.z * a.chunk;
+    const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np);
+    const long long N = a.N;
+    const real omega = real(a.omega), tau = real(a.tau), T0 = real(a.T0);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+
+    // interior site of this thread in region coordinates
+    const int rxi = tx + 1, ryi = (D == 3) ? ty + 1 : 0;
+    // ring site of this thread (if tid < NRING)
+    int rxr = 0, ryr = 0;
+    if (tid < NRING) {
+        if (D < 3) {
+            rxr = (tid == 0) ? 0 : RX - 1;
+        } else if (tid < RX) {
+            rxr = tid;
+            ryr = 0;
+        } else if (tid < 2 * RX) {
+            rxr = tid - RX;
+            ryr = Sh::RY - 1;
+        } else if (tid < 2 * RX + TY) {
+            rxr = 0;
+            ryr = tid - 2 * RX + 1;
+        } else {
+            rxr = RX - 1;
+            ryr = tid - 2 * RX - TY + 1;
+        }
+    }
+
+    // interior values carried from stage 1 of plane p to stage 2 of plane p
+    real c_df[Q], c_bt[NB], c_rho, c_j[D], c_E;
+    real n_df[Q], n_bt[NB], n_rho, n_j[D], n_E;
+
+    double acc[D + 2];
+#pragma unroll
+    for (int k = 0; k < D + 2; ++k) acc[k] = 0.0;
+    int bad = 0;
+
+    auto slot_of = [&](int p) { return (D == 1) ? 0 : (p - p0 + 1) % 3; };
+
+    // Stage 1 for one region site.  (gx, gy, gz): unwrapped global coords.
+    // Writes u0, rho*b into aux[slot]; returns the site values if `keep`.
+    auto stage1_site = [&](int rx, int ry, int q, int slot, bool keep, real* o_df, real* o_bt,
+                           real& o_rho, real* o_j, real& o_E) {
+        int gx = x0 - 1 + rx;
+        int gy = (D == 3) ? modp(y0 - 1 + ry, ny) : (D == 2 ? q : 0);
+        int gz = (D == 3) ? q : 0;
+        const int r = rx + RX * ry;
+        const bool outside = a.fixed_x && (gx < 0 || gx >= nx);
+        if (outside) {
+            const int side = gx < 0 ? 0 : 1;
+            const long long row = gy + (long long)ny * gz;
+#pragma unroll
+            for (int k = 0; k < NAUX; ++k)
+                aux[(slot * NAUX + k) * RS + r] = gaux[((long long)side * NAUX + k) * a.rows + row];
+            return;
+        }
+        if (!a.fixed_x) gx = modp(gx, nx);
+        // pull
+        real df[Q], bsum[NB];
+        real rho = real(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) bsum[k] = real(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int sx = gx - L::e(i, 0);
+            int sy = (D >= 2) ? wrap1(gy - L::e(i, 1), ny) : 0;
+            int sz = (D == 3) ? wrap1(gz - L::e(i, 2), nz) : 0;
+            real v;
+            real bv[NB];
+            if (a.fixed_x && (sx < 0 || sx >= nx)) {
+                const int side = sx < 0 ? 0 : 1;
+                const long long row = sy + (long long)ny * sz;
+                v = gf[((long long)side * Q + i) * a.rows + row];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) bv[k] = gb[((long long)side * NB + k) * a.rows + row];
+            } else {
+                sx = wrap1(sx, nx);
+                const long long s = sx + (long long)nx * (sy + (long long)ny * sz);
+                v = Store<FS>::ld(fin, (long long)i * N + s);
+#pragma unroll
+                for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + (long long)k * N + s));
+            }
+            df[i] = v;
+            const real fi = real(L::w(i)) + v;
+            rho += v;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) bsum[k] += fi * bv[k];
+        }
+        rho += real(1);
+        const real irho = rcp(rho);
+        real j[D], bt[NB];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            j[c] = real(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::e(i, c) != 0) j[c] += real(L::e(i, c)) * df[i];
+        }
+        real trb = real(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) bt[k] = bsum[k] * irho;
+#pragma unroll
+        for (int c = 0; c < D; ++c) trb += bt[c];
+        // Ebar = sum fbar |e|^2 + rho tr bbar = sum df (|e|^2 - D/3) + rho tr bt
+        real E = rho * trb;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) E += real(norm2<D>(i) - D * (1.0 / 3.0)) * df[i];
+        real u0[D], uu = real(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            u0[c] = j[c] * irho;
+            uu += u0[c] * u0[c];
+        }
+        const real Tu = a.thermal ? (E - rho * uu) * irho * real(1.0 / D) : T0;
+        // rho*b for the gradient (Eq. 68): rho (bbar - (w/2)(bbar - b^eq(u0,Tu)))
+        // in shifted variables bt = b + I/3, bt^eq = T I + u u / 3.
+        const real hw = real(0.5) * omega;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int d2 = c; d2 < D; ++d2) {
+                const int k = sym<D>(c, d2);
+                const real beq = u0[c] * u0[d2] * real(1.0 / 3.0) + (c == d2 ? Tu : real(0));
+                real rb = rho * (bt[k] - hw * (bt[k] - beq));
+                if (c == d2) rb -= rho * real(1.0 / 3.0);
+                aux[(slot * NAUX + D + k) * RS + r] = rb;
+            }
+#pragma unroll
+        for (int c = 0; c < D; ++c) aux[(slot * NAUX + c) * RS + r] = u0[c];
+        if (keep) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) o_df[i] = df[i];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) o_bt[k] = bt[k];
+            o_rho = rho;
+#pragma unroll
+            for (int c = 0; c < D; ++c) o_j[c] = j[c];
+            o_E = E;
+        }
+    };
+
+    auto stage1 = [&](int q, bool keep_next) {
+        const int qq = (D == 1) ? 0 : modp(q, np);
+        const int slot = slot_of(q);
+        if (keep_next)
+            stage1_site(rxi, ryi, qq, slot, true, n_df, n_bt, n_rho, n_j, n_E);
+        else
+            stage1_site(rxi, ryi, qq, slot, false, n_df, n_bt, n_rho, n_j, n_E);
+        if (tid < NRING) {
+            real d_df[Q], d_bt[NB], d_rho, d_j[D], d_E;
+            stage1_site(rxr, ryr, qq, slot, false, d_df, d_bt, d_rho, d_j, d_E);
+        }
+    };
+
+    // Stage 2 for the interior site of this thread at plane p.
+    auto stage2 = [&](int p) {
+        const int gx = x0 + tx;
+        const int gy = (D == 3) ? y0 + ty : (D == 2 ? p : 0);
+        const int gz = (D == 3) ? p : 0;
+        if (gx >= nx || (D == 3 && gy >= ny)) return;
+        const long long s = gx + (long long)nx * (gy + (long long)ny * gz);
+        // gradient terms
+        real F[D], G[NB];
+#pragma unroll
+        for (int c = 0; c < D; ++c) F[c] = real(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) G[k] = real(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int em = (D == 3) ? L::e(i, 2) : (D == 2 ? L::e(i, 1) : 0);
+            const int slot = (D == 1) ? 0 : slot_of(p + em);
+            const int r = (rxi + L::e(i, 0)) + RX * ((D == 3) ? ryi + L::e(i, 1) : 0);
+            real rbn[NB], un[D];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) rbn[k] = aux[(slot * NAUX + D + k) * RS + r];
+#pragma unroll
+            for (int c = 0; c < D; ++c) un[c] = aux[(slot * NAUX + c) * RS + r];
+            real v[D];  // v_b = e_i . (rho b)_{., b}
+#pragma unroll
+            for (int b2 = 0; b2 < D; ++b2) {
+                v[b2] = real(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (L::e(i, c) != 0) v[b2] += real(L::e(i, c)) * rbn[sym<D>(c, b2)];
+            }
+            const real wi = real(L::w(i));
+#pragma unroll
+            for (int b2 = 0; b2 < D; ++b2) F[b2] += wi * v[b2];
+#pragma unroll
+            for (int b2 = 0; b2 < D; ++b2)
+#pragma unroll
+                for (int c = b2; c < D; ++c) G[sym<D>(b2, c)] += wi * (un[c] * v[b2] + un[b2] * v[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) F[c] *= real(-3);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) G[k] *= real(-3);
+        real trG = real(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) trG += G[c];
+        const real rho = c_rho, irho = rcp(rho);
+        real u[D], uu = real(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            u[c] = (c_j[c] + real(0.5) * F[c]) * irho;
+            uu += u[c] * u[c];
+        }
+        const real Ecorr = c_E + real(0.5) * trG;
+        const real Tm = (Ecorr - rho * uu) * irho * real(1.0 / D);
+        const real T = a.thermal ? Tm : T0;
+        // fatal: the method divides by rho; non-finite values propagate
+        if (!(rho > real(0)) || !isfinite(Ecorr) || !isfinite(uu)) bad |= 1;
+        // not fatal: a negative moment temperature only makes b^eq more
+        // negative (thermal mode); it occurs transiently at sharp fronts
+        if (a.thermal && !(Tm > real(0))) bad |= 2;
+        if (a.want_diag) {
+            acc[0] += double(rho);
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[1 + c] += double(c_j[c]) + 0.5 * double(F[c]);
+            acc[D + 1] += double(Ecorr);
+        }
+        if (a.mout) {
+            a.mout[s] = double(rho);
+#pragma unroll
+            for (int c = 0; c < D; ++c) a.mout[(1 + c) * N + s] = double(u[c]);
+            a.mout[(1 + D) * N + s] = double(Tm);
+        }
+        if (!a.write_state) return;
+        real feq[Q];
+        Equilibrium<D, real>::dev(rho, u, feq);
+        FS* __restrict__ fout = static_cast<FS*>(a.fout);
+        breal* __restrict__ bout = static_cast<breal*>(a.bout);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const real tgt = feq[i] + tau * forcing_term<D, real>(i, F, G, trG);
+            Store<FS>::st(fout, (long long)i * N + s, c_df[i] + omega * (tgt - c_df[i]));
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int d2 = c; d2 < D; ++d2) {
+                const int k = sym<D>(c, d2);
+                const real beq = u[c] * u[d2] * real(1.0 / 3.0) + (c == d2 ? T : real(0));
+                bout[(long long)k * N + s] = breal(c_bt[k] + omega * (beq - c_bt[k]));
+            }
+    };
+
+    auto carry = [&]() {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) c_df[i] = n_df[i];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) c_bt[k] = n_bt[k];
+        c_rho = n_rho;
+#pragma unroll
+        for (int c = 0; c < D; ++c) c_j[c] = n_j[c];
+        c_E = n_E;
+    };
+
+    if (D == 1) {
+        stage1(0, true);
+        carry();
+        __syncthreads();
+        stage2(0);
+    } else {
+        stage1(p0 - 1, false);
+        stage1(p0, true);
+        carry();
+        for (int p = p0; p < p1; ++p) {
+            stage1(p + 1, true);
+            __syncthreads();
+            stage2(p);
+            __syncthreads();
+            carry();
+        }
+    }
+
+    if (bad) atomicOr(a.flag, bad);
+
+    if (a.want_diag) {
+        // block reduction in a fixed order: warp shuffle, then warps in order
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int k = 0; k < D + 2; ++k) {
+            double v = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * (D + 2) + k] = v;
+        }
+        __syncthreads();
+        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        __shared__ bool last;
+        if (tid == 0) {
+            for (int k = 0; k < D + 2; ++k) {
+                double v = 0.0;
+                for (int w = 0; w < NT / 32; ++w) v += red[w * (D + 2) + k];
+                a.partial[(long long)bid * (D + 2) + k] = v;
+            }
+            __threadfence();
+            last = (atomicAdd(a.ticket, 1u) == nblocks - 1);
+        }
+        __syncthreads();
+        if (last) {
+            // The last block sums the per-block partials: thread t takes
+            // blocks t, t + NT, ... in order, then the same fixed tree as
+            // above -- the result does not depend on block scheduling.
+            __threadfence();
+            double v[D + 2];
+#pragma unroll
+            for (int k = 0; k < D + 2; ++k) v[k] = 0.0;
+            for (unsigned int b2 = tid; b2 < nblocks; b2 += NT)
+#pragma unroll
+                for (int k = 0; k < D + 2; ++k) v[k] += __ldcg(a.partial + (long long)b2 * (D + 2) + k);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < D + 2; ++k) {
+                double x = v[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) red[warp * (D + 2) + k] = x;
+            }
+            __syncthreads();
+            double tot = 0.0;
+            if (tid < D + 2)
+                for (int w = 0; w < NT / 32; ++w) tot += red[w * (D + 2) + tid];
+            __syncthreads();
+            if (tid < D + 2) red[tid] = tot;
+            __syncthreads();
+            if (tid == 0) {
+                const long long st = *a.step_ctr;
+                if (a.diag_out)
+                    for (int k = 0; k < D + 2; ++k) a.diag_out[k] = red[k];
+                if (a.hist) {
+                    double* rec = a.hist + (st % a.hist_cap) * (D + 3);
+                    rec[0] = double(st);
+                    for (int k = 0; k < D + 2; ++k) rec[1 + k] = red[k];
+                }
+                if (a.write_state) *a.step_ctr = st + 1;
+                *a.ticket = 0u;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Start: every site emits its local equilibrium, df = f^eq(rho, u) - w,
+// bt = b^eq(u, T) + I/3 = T I + u u / 3 (Eq. 36, Appendix A).
+template <int D, typename FS>
+__global__ void init_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                            const double* __restrict__ T, FS* __restrict__ f,
+                            typename Store<FS>::breal* __restrict__ b, long long N) {
+    using L = Lattice<D>;
+    using real = typename Store<FS>::real;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    real uu[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) uu[c] = real(u[c * N + s]);
+    real df[L::Q];
+    Equilibrium<D, real>::dev(real(rho[s]), uu, df);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Store<FS>::st(f, i * N + s, df[i]);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int d2 = c; d2 < D; ++d2)
+            b[sym<D>(c, d2) * N + s] = uu[c] * uu[d2] * real(1.0 / 3.0) + (c == d2 ? real(T[s]) : real(0));
+}
+
+// Reservoirs of the fixed-state boundary: for each row, the equilibrium of the
+// edge site's initial state (side 0: x = 0, side 1: x = nx - 1).
+template <int D, typename R>
+__global__ void reservoir_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                                 const double* __restrict__ T, int nx, long long rows, long long N,
+                                 R* __restrict__ gf, R* __restrict__ gb, R* __restrict__ gaux) {
+    using L = Lattice<D>;
+    constexpr int NB = L::NB, NAUX = D + NB;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 2 * rows) return;
+    const int side = (int)(t / rows);
+    const long long row = t % rows;
+    const long long s = (side ? nx - 1 : 0) + (long long)nx * row;
+    R uu[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) uu[c] = R(u[c * N + s]);
+    const R r = R(rho[s]), TT = R(T[s]);
+    R df[L::Q];
+    Equilibrium<D, R>::dev(r, uu, df);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) gf[((long long)side * L::Q + i) * rows + row] = df[i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) gaux[((long long)side * NAUX + c) * rows + row] = uu[c];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int d2 = c; d2 < D; ++d2) {
+            const int k = sym<D>(c, d2);
+            const R bt = uu[c] * uu[d2] * R(1.0 / 3.0) + (c == d2 ? TT : R(0));
+            gb[((long long)side * NB + k) * rows + row] = bt;
+            // rho*b of a site at equilibrium: rho (b^eq) = rho (bt - I/3)
+            gaux[((long long)side * NAUX + D + k) * rows + row] = r * (bt - (c == d2 ? R(1.0 / 3.0) : R(0)));
+        }
+}
+
+// Emitted state <-> FP64 planes of fbar*_i and bbar* (unshifted).
+template <int D, typename FS>
+__global__ void get_state_kernel(const FS* __restrict__ f, const typename Store<FS>::breal* __restrict__ b,
+                                 double* __restrict__ fo, double* __restrict__ bo, long long N) {
+    using L = Lattice<D>;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if (fo)
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) fo[i * N + s] = L::w(i) + double(Store<FS>::ld(f, i * N + s));
+    if (bo)
+#pragma unroll
+        for (int k = 0; k < L::NB; ++k) bo[k * N + s] = double(b[k * N + s]) - (k < D ? 1.0 / 3.0 : 0.0);
+}
+
+template <int D, typename FS>
+__global__ void set_state_kernel(FS* __restrict__ f, typename Store<FS>::breal* __restrict__ b,
+                                 const double* __restrict__ fi, const double* __restrict__ bi, long long N) {
+    using L = Lattice<D>;
+    using breal = typename Store<FS>::breal;
+    using real = typename Store<FS>::real;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    if (fi)
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) Store<FS>::st(f, i * N + s, real(fi[i * N + s] - L::w(i)));
+    if (bi)
+#pragma unroll
+        for (int k = 0; k < L::NB; ++k) b[k * N + s] = breal(bi[k * N + s] + (k < D ? 1.0 / 3.0 : 0.0));
+}
+
+}  // namespace lbm

@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/lbm.h (liblbm.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Functions keep the C names (lbm_create, lbm_init, lbm_step, ...);
+``Simulation`` is a small convenience wrapper that owns a handle and moves
+numpy arrays in and out.  Importing this module fails loudly if liblbm.so
+has not been built -- there is no CPU fallback.
+
+Field shapes follow the library's layout: rho and T are (nz, ny, nx), u is
+(d, nz, ny, nx); populations are (Q, nz, ny, nx) and the variance tensor
+(nb, nz, ny, nx).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUSY, LBM_EIO = range(8)
+LBM_BC_PERIODIC, LBM_BC_FIXED_STATE = 0, 1
+LBM_F64, LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
+BCS = {"periodic": LBM_BC_PERIODIC, "fixed": LBM_BC_FIXED_STATE}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class lbm_opts(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int),
+        ("thermal", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+        ("tile", ctypes.c_int),
+        ("chunk", ctypes.c_int),
+        ("steps_per_launch", ctypes.c_int),
+        ("diagnostics", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
+    ]
+
+
+class lbm_fields_in(ctypes.Structure):
+    _fields_ = [("rho", ctypes.POINTER(ctypes.c_double)),
+                ("u", ctypes.POINTER(ctypes.c_double)),
+                ("T", ctypes.POINTER(ctypes.c_double))]
+
+
+class lbm_fields_out(ctypes.Structure):
+    _fields_ = [("rho", ctypes.POINTER(ctypes.c_double)),
+                ("u", ctypes.POINTER(ctypes.c_double)),
+                ("T", ctypes.POINTER(ctypes.c_double))]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbm.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_2501_00620_gb300.build); the CUDA library is required")
+    L = ctypes.CDLL(LIB_PATH)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    L.lbm_default_opts.argtypes = [ctypes.POINTER(lbm_opts)]
+    L.lbm_default_opts.restype = None
+    L.lbm_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.POINTER(vp)]
+    L.lbm_create_ex.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                     ctypes.POINTER(lbm_opts), ctypes.POINTER(vp)]
+    L.lbm_init.argtypes = [vp, ctypes.POINTER(lbm_fields_in)]
+    L.lbm_step.argtypes = [vp, ctypes.c_long]
+    L.lbm_sync.argtypes = [vp]
+    L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
+    L.lbm_diagnostics.argtypes = [vp, dp]
+    L.lbm_diagnostics_history.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_last_diagnostics.argtypes = [vp, dp]
+    L.lbm_get_state.argtypes = [vp, dp, dp]
+    L.lbm_set_state.argtypes = [vp, dp, dp]
+    L.lbm_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_flags.restype = ctypes.c_int
+    L.lbm_step_count.argtypes = [vp]
+    L.lbm_step_count.restype = ctypes.c_long
+    L.lbm_save.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_load.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_version.restype = ctypes.c_char_p
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_sync", "lbm_moments",
+                 "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
+                 "lbm_save", "lbm_load"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(status):
+    if status != LBM_OK:
+        raise LBMError(status, _lib.lbm_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+# --- C names -----------------------------------------------------------------
+
+def lbm_version():
+    return _lib.lbm_version().decode()
+
+
+def lbm_default_opts():
+    o = lbm_opts()
+    _lib.lbm_default_opts(ctypes.byref(o))
+    return o
+
+
+def lbm_create(dim, nx, ny, nz, tau, T0, bc=LBM_BC_PERIODIC, opts=None):
+    h = ctypes.c_void_p()
+    if opts is None:
+        _check(_lib.lbm_create(dim, nx, ny, nz, tau, T0, bc, ctypes.byref(h)))
+    else:
+        _check(_lib.lbm_create_ex(dim, nx, ny, nz, tau, T0, bc, ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def lbm_init(sim, rho, u, T):
+    fi = lbm_fields_in(_dp(rho), _dp(u), _dp(T))
+    _check(_lib.lbm_init(sim, ctypes.byref(fi)))
+
+
+def lbm_step(sim, n):
+    _check(_lib.lbm_step(sim, int(n)))
+
+
+def lbm_sync(sim):
+    _check(_lib.lbm_sync(sim))
+
+
+def lbm_moments(sim, rho, u, T):
+    fo = lbm_fields_out(_dp(rho), _dp(u), _dp(T))
+    _check(_lib.lbm_moments(sim, ctypes.byref(fo)))
+
+
+def lbm_diagnostics(sim, out):
+    _check(_lib.lbm_diagnostics(sim, _dp(out)))
+
+
+def lbm_diagnostics_history(sim, out, cap):
+    n = ctypes.c_int()
+    _check(_lib.lbm_diagnostics_history(sim, _dp(out), int(cap), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_last_diagnostics(sim, out):
+    _check(_lib.lbm_last_diagnostics(sim, _dp(out)))
+
+
+def lbm_get_state(sim, f, b):
+    _check(_lib.lbm_get_state(sim, _dp(f), _dp(b)))
+
+
+def lbm_set_state(sim, f, b):
+    _check(_lib.lbm_set_state(sim, _dp(f), _dp(b)))
+
+
+def lbm_flags(sim):
+    v = ctypes.c_int()
+    _check(_lib.lbm_flags(sim, ctypes.byref(v)))
+    return v.value
+
+
+def lbm_step_count(sim):
+    return _lib.lbm_step_count(sim)
+
+
+def lbm_save(sim, path):
+    _check(_lib.lbm_save(sim, os.fsencode(path)))
+
+
+def lbm_load(sim, path):
+    _check(_lib.lbm_load(sim, os.fsencode(path)))
+
+
+def lbm_destroy(sim):
+    _lib.lbm_destroy(sim)
+
+
+# --- convenience wrapper -------------------------------------------------------
+
+def n_q(d):
+    return {1: 3, 2: 9, 3: 19}[d]
+
+
+def n_b(d):
+    return {1: 1, 2: 3, 3: 6}[d]
+
+
+class TorchAllocator:
+    """Device allocator callbacks backed by PyTorch's caching allocator."""
+
+    def __init__(self, device=0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self._alloc = ALLOC_FN(self._a)
+        self._free = FREE_FN(self._f)
+
+    def _a(self, nbytes, ctx):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device)
+        except Exception:
+            return None
+
+    def _f(self, ptr, nbytes, ctx):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+class Simulation:
+    """One lattice on the GPU.  dims = (nx, ny, nz); unused extents are 1."""
+
+    def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
+                 thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
+                 use_graphs=True, torch_allocator=False):
+        self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.Q, self.nb = n_q(dim), n_b(dim)
+        o = lbm_default_opts()
+        o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        o.thermal = int(bool(thermal))
+        o.device = device
+        o.stream = stream
+        o.tile = tile
+        o.chunk = chunk
+        o.diagnostics = int(bool(diagnostics))
+        o.use_graphs = int(bool(use_graphs))
+        self._allocator = None
+        if torch_allocator:
+            self._allocator = TorchAllocator(device)
+            o.alloc = self._allocator._alloc
+            o.free = self._allocator._free
+        self._opts = o
+        self.h = lbm_create(dim, nx, ny, nz, tau, T0, BCS[bc] if isinstance(bc, str) else bc, o)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, u, T):
+        rho = np.ascontiguousarray(np.broadcast_to(rho, self.shape), dtype=np.float64)
+        T = np.ascontiguousarray(np.broadcast_to(T, self.shape), dtype=np.float64)
+        u = np.ascontiguousarray(np.broadcast_to(u, (self.dim,) + self.shape), dtype=np.float64)
+        lbm_init(self.h, rho, u, T)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def flags(self):
+        return lbm_flags(self.h)
+
+    @property
+    def nstep(self):
+        return lbm_step_count(self.h)
+
+    def moments(self):
+        rho = np.empty(self.shape)
+        u = np.empty((self.dim,) + self.shape)
+        T = np.empty(self.shape)
+        lbm_moments(self.h, rho, u, T)
+        return rho, u, T
+
+    def diagnostics(self):
+        out = np.empty(self.dim + 2)
+        lbm_diagnostics(self.h, out)
+        return out
+
+    def diagnostics_history(self, cap=4096):
+        out = np.empty((cap, self.dim + 3))
+        n = lbm_diagnostics_history(self.h, out, cap)
+        return out[:n]
+
+    def last_diagnostics(self):
+        out = np.empty(self.dim + 3)
+        lbm_last_diagnostics(self.h, out)
+        return out
+
+    def emitted(self):
+        f = np.empty((self.Q,) + self.shape)
+        b = np.empty((self.nb,) + self.shape)
+        lbm_get_state(self.h, f, b)
+        return f, b
+
+    def set_emitted(self, f, b):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        lbm_set_state(self.h, f, b)
+
+    def save(self, path):
+        lbm_save(self.h, path)
+
+    def load(self, path):
+        lbm_load(self.h, path)

@@ -12,12 +12,16 @@ Temperature scales (lattice units, c^2 = 1):
 * 1D sound wave: T0 = 1/3, where the equilibrium bump width b^eq vanishes at
   rest (the standard-lattice limit).
 * 1D two-state Riemann problem: the stated temperatures 1.0 and 0.8 are in
-  units of T_UNIT_RIEMANN = 0.12 c^2.  With the pressure ratio of 10 the
-  scheme is stable only in a narrow window of the temperature scale (about
-  0.1-0.15 c^2 at tau = 0.55; lower T makes the finite-difference correction
-  at the jump drive T negative, higher T brings the shock near the lattice
-  speed).  The shock then moves about 0.79 cells per step and reaches the
-  right reservoir of a 4096-cell line after about 2600 steps.
+  units of T_UNIT_RIEMANN = 0.15 c^2.  With the pressure ratio of 10 the
+  scheme is usable only in a narrow window of the temperature scale at
+  tau = 0.55: below about 0.1 c^2 the finite-difference correction at the jump
+  drives T negative within tens of steps; from 0.1 to 0.14 c^2 the run
+  survives but, once the waves reach the frozen reservoirs, perturbations
+  grow (a 1e-13 change in the start grows to ~1e-9 by step 4600 at 0.12);
+  above 0.15 the shock approaches the lattice speed and the run fails.  At
+  0.15 a 1e-6 perturbation stays at 1e-6 over 5000 steps.  The shock moves
+  about 0.88 cells per step and reaches the right reservoir of a 4096-cell
+  line after about 2300 steps.
 * 2D Taylor-Green + pulse: T0 = 0.1 c^2.
 * 3D solenoidal field: T0 = 0.05 c^2 (the paper's lowest temperature).
 """
@@ -25,7 +29,7 @@ import math
 
 import numpy as np
 
-T_UNIT_RIEMANN = 0.12
+T_UNIT_RIEMANN = 0.15
 
 
 def _shape(d, nx, ny, nz):

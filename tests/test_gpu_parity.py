@@ -1,0 +1,307 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances:
+* FP64 storage: 1e-12 norm-wise (max |gpu - oracle| / max |oracle| per field)
+  on rho, T and the emitted populations, and 1e-12 on u in units of the
+  lattice speed c, after the full step counts of the 1D configurations and
+  after tens of steps on multi-tile 2D/3D lattices.  The only differences are
+  rounding order and fused multiply-adds.  u is a difference of O(1)
+  populations divided by rho, so its round-off floor is absolute (~1e-16 c
+  per step): for the 1D sound wave (|u| ~ 6e-4 c) the two sides' rounding
+  alone reaches ~2e-12 relative to max|u| after a few hundred steps.
+* FP32 / FP16 / BF16 storage: one step from an identical emitted state, the
+  populations must agree to the storage precision (FP32 2e-6, FP16 2e-3,
+  BF16 1.6e-2 of the population scale); longer runs are reported, bounded
+  loosely.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from _parity import check_windows, normwise
+from paper_2501_00620_gb300 import workloads as W
+
+try:
+    from paper_2501_00620_gb300 import lbm
+except ImportError as _e:  # collected where the library is not built; the tests then fail loudly
+    lbm = None
+    _IMPORT_ERROR = _e
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _library_loaded():
+    if lbm is None:
+        raise _IMPORT_ERROR
+
+FP64_TOL = 1e-12
+
+
+def run_pair(d, shape, fields, tau, T0, thermal, bc, steps, dtype="f64", **kw):
+    nz, ny, nx = shape
+    g = lbm.Simulation(d, nx, ny, nz, tau=tau, T0=T0, bc=bc, dtype=dtype, thermal=thermal, **kw)
+    g.init(*fields)
+    o = oracle.Sim(d, nx, ny, nz, tau=tau, T0=T0, thermal=thermal, bc=bc)
+    o.init(*fields)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def assert_fp64_parity(g, o, tol=FP64_TOL):
+    gr, gu, gT = g.moments()
+    orr, ou, oT = o.moments()
+    assert normwise(gr, orr) < tol
+    assert np.abs(gu - ou).max() < tol          # units of c = 1
+    assert normwise(gT, oT) < tol
+    gf, gb = g.emitted()
+    of, ob = o.emitted()
+    assert normwise(gf, of) < tol
+    # bbar is stored as bbar + c^2/3 (the full per-axis variance), so its
+    # round-off floor is absolute in units of c^2 (bbar ~ 1e-10 at T = c^2/3)
+    assert np.abs(gb - ob).max() < tol
+
+
+def test_sound1d_full_fp64():
+    c = W.CONFIGS["sound1d"]
+    g, o = run_pair(1, (1, 1, c["nx"]), W.fields_for("sound1d"), c["tau"], c["T0"], c["thermal"],
+                    c["bc"], c["steps"])
+    assert_fp64_parity(g, o)
+
+
+def test_riemann1d_full_fp64():
+    c = W.CONFIGS["riemann1d"]
+    g, o = run_pair(1, (1, 1, c["nx"]), W.fields_for("riemann1d"), c["tau"], c["T0"], c["thermal"],
+                    c["bc"], c["steps"])
+    assert_fp64_parity(g, o)
+    # the first step after the start has a transiently negative moment
+    # temperature at the jump (the oracle shows the same): reported, not fatal
+    assert g.flags() == 2
+
+
+def test_riemann1d_fp32_error():
+    """Config 2 with FP32 populations against the FP64 oracle after 5000 steps."""
+    c = W.CONFIGS["riemann1d"]
+    g, o = run_pair(1, (1, 1, c["nx"]), W.fields_for("riemann1d"), c["tau"], c["T0"], c["thermal"],
+                    c["bc"], c["steps"], dtype="f32")
+    gr, gu, gT = g.moments()
+    orr, ou, oT = o.moments()
+    assert normwise(gr, orr) < 1e-4 and normwise(gu, ou) < 1e-3 and normwise(gT, oT) < 1e-4
+
+
+@pytest.mark.parametrize("thermal,bc", [(True, "periodic"), (False, "periodic"), (True, "fixed")])
+def test_2d_ragged_fp64(thermal, bc):
+    """D2Q9 on 300 x 70 (tiles of 128-512 plus a ragged tail; several chunks)."""
+    nx, ny = 300, 70
+    if bc == "fixed":
+        rho, u, T = W.riemann_1d(nx)
+        rho = np.repeat(rho, ny, axis=1)
+        T = np.repeat(T, ny, axis=1)
+        u = np.zeros((2, 1, ny, nx))
+        T0 = W.T_UNIT_RIEMANN
+        tau = 0.55
+    else:
+        r, uu, TT = W.taylor_green_pulse_2d(300)
+        rho, T = r[:, :ny, :], TT[:, :ny, :]
+        u = uu[:, :, :ny, :]
+        T0, tau = 0.1, 0.6
+    g, o = run_pair(2, (1, ny, nx), (rho, u, T), tau, T0, thermal, bc, 60)
+    assert_fp64_parity(g, o)
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+def test_3d_ragged_fp64(thermal):
+    """D3Q19 on 40 x 20 x 24 (x, y tiles with ragged tails, several z chunks)."""
+    rho, u, T = W.solenoidal_3d(40, k0=2.0, T0=0.05, thermal=thermal)
+    rho, T, u = rho[:24, :20, :], T[:24, :20, :], u[:, :24, :20, :]
+    g, o = run_pair(3, (24, 20, 40), (rho, u, T), 0.52, 0.05, thermal, "periodic", 20)
+    assert_fp64_parity(g, o)
+
+
+def test_3d_fixed_state_fp64():
+    nx, ny, nz = 36, 10, 6
+    rho, _, T = W.riemann_1d(nx)
+    rho = np.broadcast_to(rho, (nz, ny, nx)).copy()
+    T = np.broadcast_to(T, (nz, ny, nx)).copy()
+    g, o = run_pair(3, (nz, ny, nx), (rho, np.zeros((3, nz, ny, nx)), T), 0.55, W.T_UNIT_RIEMANN,
+                    True, "fixed", 15)
+    assert_fp64_parity(g, o)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_tiny_lattices(d):
+    """Degenerate extents (1 and 2 sites per axis) wrap correctly."""
+    shape = {1: (1, 1, 2), 2: (1, 1, 5), 3: (2, 1, 3)}[d]
+    rng = np.random.default_rng(d)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.05 * rng.standard_normal((d,) + shape)
+    g, o = run_pair(d, shape, (rho, u, 0.2), 0.7, 0.2, True, "periodic", 10)
+    assert_fp64_parity(g, o)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_variants_and_chunks(d):
+    """For a given tile variant every chunk length gives the same bits; the
+    tile variants (separate template instantiations, where the compiler may
+    contract multiply-adds differently) agree to a few units in the last
+    place."""
+    shape = (1, 33, 70) if d == 2 else (13, 11, 37)
+    rng = np.random.default_rng(0)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((d,) + shape)
+    ref = None
+    nv = 4 if d == 3 else 3
+    for v in range(nv):
+        vref = None
+        for chunk in (1, 5, 64):
+            g = lbm.Simulation(d, shape[2], shape[1], shape[0], tau=0.6, T0=0.1, thermal=True,
+                               tile=v, chunk=chunk)
+            g.init(rho, u, 0.1)
+            g.step(7)
+            f, b = g.emitted()
+            if vref is None:
+                vref = (f, b)
+            else:
+                assert np.array_equal(f, vref[0]) and np.array_equal(b, vref[1])
+        if ref is None:
+            ref = vref
+        else:
+            assert np.abs(vref[0] - ref[0]).max() < 1e-15 and np.abs(vref[1] - ref[1]).max() < 1e-15
+
+
+def test_graphs_equal_direct_launches():
+    rho, u, T = W.taylor_green_pulse_2d(64)
+    out = []
+    for graphs in (True, False):
+        g = lbm.Simulation(2, 64, 64, tau=0.6, T0=0.1, thermal=True, use_graphs=graphs)
+        g.init(rho, u, T)
+        g.step(37)
+        g.step(40)
+        out.append(g.emitted())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_diagnostics_vs_oracle_and_conservation():
+    rng = np.random.default_rng(3)
+    shape = (6, 10, 12)
+    rho = 1 + 0.1 * rng.random(shape)
+    u = 0.05 * rng.standard_normal((3,) + shape)
+    T = 0.1 * (1 + 0.1 * rng.random(shape))
+    g, o = run_pair(3, shape, (rho, u, T), 0.6, 0.1, True, "periodic", 0)
+    d0 = g.diagnostics()
+    np.testing.assert_allclose(d0, o.diagnostics(), rtol=1e-13, atol=1e-13 * d0[0])
+    g.step(200)
+    o.step(200)
+    d1 = g.diagnostics()
+    np.testing.assert_allclose(d1, o.diagnostics(), rtol=1e-12, atol=1e-12 * d0[0])
+    assert abs(d1[0] - d0[0]) / d0[0] < 1e-13
+    assert np.abs(d1[1:4] - d0[1:4]).max() / d0[0] < 1e-13
+    assert abs(d1[4] - d0[4]) / d0[4] < 1e-12
+    # the per-step history recorded by the step kernel
+    h = g.diagnostics_history()
+    assert len(h) == 200 and h[0, 0] == 0 and h[-1, 0] == 199
+    assert np.abs(h[:, 1] - d0[0]).max() / d0[0] < 1e-13
+
+
+def test_checkpoint_resume_bitwise():
+    rho, u, T = W.taylor_green_pulse_2d(96)
+    a = lbm.Simulation(2, 96, 96, tau=0.6, T0=0.1, thermal=True, dtype="f32")
+    a.init(rho, u, T)
+    a.step(30)
+    b = lbm.Simulation(2, 96, 96, tau=0.6, T0=0.1, thermal=True, dtype="f32")
+    b.init(rho, u, T)
+    b.step(15)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "ck.bin")
+        b.save(p)
+        c = lbm.Simulation(2, 96, 96, tau=0.6, T0=0.1, thermal=True, dtype="f32")
+        c.load(p)
+    c.step(15)
+    fa, ba = a.emitted()
+    fc, bc_ = c.emitted()
+    assert np.array_equal(fa, fc) and np.array_equal(ba, bc_)
+    assert c.nstep == 30
+
+
+def test_state_roundtrip():
+    rho, u, T = W.taylor_green_pulse_2d(32)
+    g = lbm.Simulation(2, 32, 32, tau=0.6, T0=0.1, thermal=True)
+    g.init(rho, u, T)
+    g.step(3)
+    f, b = g.emitted()
+    h = lbm.Simulation(2, 32, 32, tau=0.6, T0=0.1, thermal=True)
+    h.init(rho, u, T)
+    h.set_emitted(f, b)
+    f2, b2 = h.emitted()
+    assert np.array_equal(f, f2) and np.array_equal(b, b2)
+
+
+def test_unstable_state_is_reported_not_faulted():
+    """A violent start (u ~ c at T << 1/3) drives T negative; the library
+    reports LBM_EUNSTABLE and the process keeps a working context."""
+    n = 64
+    u = np.zeros((1, 1, 1, n))
+    u[0, 0, 0, : n // 2] = 0.9
+    g = lbm.Simulation(1, n, tau=0.55, T0=0.02, thermal=True)
+    g.init(1.0, u, 0.02)
+    g.step(50)
+    with pytest.raises(lbm.LBMError) as e:
+        g.sync()
+    assert e.value.status == lbm.LBM_EUNSTABLE
+    g.close()
+    ok = lbm.Simulation(1, 16, tau=0.8, T0=1 / 3)
+    ok.init(1.0, np.zeros((1, 1, 1, 16)), 1 / 3)
+    ok.step(5)
+    ok.sync()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 2e-6), ("f16", 2e-3), ("bf16", 1.6e-2)])
+def test_one_step_storage_precision_2d(dtype, tol):
+    """From an identical emitted state, one GPU step in the storage dtype
+    matches the oracle's FP64 step to the storage precision."""
+    rho, u, T = W.taylor_green_pulse_2d(256)
+    g = lbm.Simulation(2, 256, 256, tau=0.6, T0=0.1, thermal=True, dtype=dtype)
+    g.init(rho, u, T)
+    g.step(5)
+    f0, b0 = g.emitted()
+    g.step(1)
+    f1, b1 = g.emitted()
+    wf, wb = check_windows(2, f0, b0, f1, b1, 0.6, 0.1, True)
+    assert wf < tol and wb < max(tol, 2e-6)
+
+
+@pytest.mark.parametrize("name", ["tgv2d", "turb3d"])
+def test_full_size_sampled_windows(name):
+    """The configurations the benchmark times (full size, FP32, autotuned
+    launch): after a few steps, random windows of the GPU state are advanced
+    one step by the oracle and compared with the GPU's next state."""
+    c = W.CONFIGS[name]
+    rho, u, T = W.fields_for(name)
+    g = lbm.Simulation(c["d"], c["nx"], c["ny"], c["nz"], tau=c["tau"], T0=c["T0"],
+                       thermal=c["thermal"], dtype=c["dtype"])
+    g.init(rho, u, T)
+    g.step(4)
+    f0, b0 = g.emitted()
+    g.step(1)
+    f1, b1 = g.emitted()
+    wf, wb = check_windows(c["d"], f0, b0, f1, b1, c["tau"], c["T0"], c["thermal"], n_windows=8)
+    assert wf < 2e-6 and wb < 2e-6
+    d = g.diagnostics()
+    assert np.isfinite(d).all()
+
+
+def test_full_size_2d_fp64_windows():
+    c = W.CONFIGS["tgv2d"]
+    rho, u, T = W.fields_for("tgv2d")
+    g = lbm.Simulation(2, c["nx"], c["ny"], tau=c["tau"], T0=c["T0"], thermal=c["thermal"], dtype="f64")
+    g.init(rho, u, T)
+    g.step(3)
+    f0, b0 = g.emitted()
+    g.step(1)
+    f1, b1 = g.emitted()
+    wf, wb = check_windows(2, f0, b0, f1, b1, c["tau"], c["T0"], c["thermal"], n_windows=8)
+    assert wf < FP64_TOL and wb < FP64_TOL

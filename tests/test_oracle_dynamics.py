@@ -213,7 +213,7 @@ def test_thermal_sound_speed():
 
 def test_riemann_converges_to_exact_gamma3():
     """Two-state Riemann data of config 2 (rho 1 : 0.125, T 1.0 : 0.8 in units
-    of 0.12 c^2, tau = 0.55, fixed-state ends): the L1 error against the exact
+    of 0.15 c^2, tau = 0.55, fixed-state ends): the L1 error against the exact
     gamma = 3 solution falls with resolution (steps = N/2, before any wave
     reaches a reservoir), and gamma = 3 fits far better than gamma = 5/3."""
     Tu = W.T_UNIT_RIEMANN
