@@ -1,0 +1,33 @@
+// Launch arguments shared by the step kernels.
+#pragma once
+
+namespace lbm {
+
+struct StepArgs {
+    const void* fin;      // Q planes, storage type: emitted df at t
+    const void* bin;      // NB planes, breal: emitted bt at t
+    void* fout;           // Q planes: emitted df at t+1 (write_state)
+    void* bout;           // NB planes
+    int nx, ny, nz;
+    int chunk;            // planes per block along the march axis
+    long long N;
+    double omega, tau, T0;
+    int thermal;
+    int fixed_x;          // 1: frozen reservoirs outside [0, nx)
+    long long rows;       // ny * nz (reservoir rows)
+    const void* gf;       // reservoirs, real: [2][Q][rows] df
+    const void* gb;       // [2][NB][rows] bt
+    const void* gaux;     // [2][D+NB][rows] u (D), rho*b (NB)
+    int write_state;      // 1: collide and store S(t+1)
+    double* mout;         // if non-null: rho (N), u (D*N), T (N) in FP64
+    int want_diag;        // 1: reduce mass, momentum, energy of the state at t
+    double* partial;      // [gridDim total][D+2] per-block sums
+    unsigned int* ticket; // completion counter for the last-block reduction
+    double* diag_out;     // if non-null: the D+2 global sums
+    double* hist;         // history ring: records of D+3 doubles
+    int hist_cap;
+    long long* step_ctr;  // device step counter (history index)
+    int* flag;            // bit 0: fatal (rho <= 0 or non-finite); bit 1: T <= 0 seen
+};
+
+}  // namespace lbm

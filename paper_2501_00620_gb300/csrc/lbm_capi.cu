@@ -2,8 +2,11 @@
 // objects, device buffers (A-B ping-pong of the emitted state), the tile /
 // chunk autotuner, CUDA-graph replay of step sequences, moments,
 // diagnostics and checkpoints.  See include/lbm.h for the contract.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -77,6 +80,8 @@ struct lbm_sim {
     // graphs: [parity of cur] -> executable graph of kGraphSteps launches
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_steps = 0;
+    // tensor maps of the TMA-staged kernel: variant -> per input buffer (f, b)
+    std::map<int, std::array<std::pair<CUtensorMap, CUtensorMap>, 2>> tmaps;
     std::vector<std::pair<void*, size_t>> allocs;
 
     void* dalloc(size_t bytes) {
@@ -135,6 +140,104 @@ StepArgs base_args(const lbm_sim* s) {
     return a;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The TMA-staged kernel needs FP32/16-bit storage, tiles that divide the
+// extents, and rows whose byte length is a multiple of 16 (tensor strides).
+bool tma_applicable(const lbm_sim* s, int v) {
+    if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64) return false;
+    if (v - kTmaBase >= n_tma_variants(s->D)) return false;
+    Variant t = variant(s->D, v);
+    if (s->nx % t.tx != 0) return false;
+    if (s->D == 3 && s->ny % t.ty != 0) return false;
+    if ((s->nx * fbytes_of(s->dtype)) % 16 != 0 || (s->nx * 4) % 16 != 0) return false;
+    if (s->nx < 2 || (s->D == 3 && s->ny < 2)) return false;
+    // the march index wraps with one conditional add or subtract
+    if ((s->D == 3 ? s->nz : s->ny) < 4) return false;
+    return encode_fn() != nullptr;
+}
+
+lbm_status tma_maps(lbm_sim* s, int v, int buf, TmaArgs* ta) {
+    auto it = s->tmaps.find(v);
+    if (it == s->tmaps.end()) {
+        TmaBox box{};
+        CK(tma_box(s->D, s->dtype, v, &box));
+        std::array<std::pair<CUtensorMap, CUtensorMap>, 2> maps{};
+        auto enc = encode_fn();
+        const cuuint64_t es = fbytes_of(s->dtype);
+        const CUtensorMapDataType dt = s->dtype == DT_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                       : s->dtype == DT_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        const cuuint64_t nx = s->nx, ny = s->ny, nz = s->nz, N = s->N;
+        for (int k = 0; k < 2; ++k) {
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUresult r1, r2;
+            if (s->D == 3) {
+                cuuint64_t gd[4] = {nx, ny, nz, (cuuint64_t)s->Q};
+                cuuint64_t gs[3] = {nx * es, nx * ny * es, N * es};
+                cuuint32_t bx[4] = {(cuuint32_t)box.sxf, (cuuint32_t)box.sy, 1, 1};
+                r1 = enc(&maps[k].first, dt, 4, s->f[k], gd, gs, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                cuuint64_t gdb[4] = {nx, ny, nz, (cuuint64_t)s->NB};
+                cuuint64_t gsb[3] = {nx * 4, nx * ny * 4, N * 4};
+                cuuint32_t bxb[4] = {(cuuint32_t)box.sxb, (cuuint32_t)box.sy, 1, (cuuint32_t)s->NB};
+                r2 = enc(&maps[k].second, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->b[k], gdb, gsb, bxb, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                cuuint64_t gd[3] = {nx, ny, (cuuint64_t)s->Q};
+                cuuint64_t gs[2] = {nx * es, N * es};
+                cuuint32_t bx[3] = {(cuuint32_t)box.sxf, 1, 1};
+                r1 = enc(&maps[k].first, dt, 3, s->f[k], gd, gs, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                cuuint64_t gdb[3] = {nx, ny, (cuuint64_t)s->NB};
+                cuuint64_t gsb[2] = {nx * 4, N * 4};
+                cuuint32_t bxb[3] = {(cuuint32_t)box.sxb, 1, (cuuint32_t)s->NB};
+                r2 = enc(&maps[k].second, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->b[k], gdb, gsb, bxb, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
+            if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+                return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " +
+                                           std::to_string((int)r2) + ")");
+        }
+        it = s->tmaps.emplace(v, maps).first;
+    }
+    ta->fmap = it->second[buf].first;
+    ta->bmap = it->second[buf].second;
+    return LBM_OK;
+}
+
+// Launch variant v with arguments a; `buf` is the input buffer (a.fin).
+lbm_status launch_variant(lbm_sim* s, int v, const StepArgs& a, int buf) {
+    if (v >= kTmaBase) {
+        TmaArgs ta;
+        lbm_status st = tma_maps(s, v, buf, &ta);
+        if (st != LBM_OK) return st;
+        ta.s = a;
+        CK(launch_step_tma(s->D, s->dtype, v, ta, s->stream));
+    } else {
+        CK(launch_step(s->D, s->dtype, v, a, s->stream));
+    }
+    return LBM_OK;
+}
+
 size_t blocks_of(const lbm_sim* s, int v, int chunk) {
     dim3 g = step_grid(s->D, v, s->nx, s->ny, s->nz, chunk);
     return (size_t)g.x * g.y * g.z;
@@ -146,7 +249,7 @@ std::vector<int> chunk_candidates(const lbm_sim* s) {
     int np = s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1);
     if (s->D == 1) return {1};
     std::vector<int> c;
-    for (int k : {8, 16, 32, 64, 128, 256}) {
+    for (int k : {8, 12, 16, 24, 32, 64, 128, 256}) {
         if (k >= np) {
             c.push_back(np);
             break;
@@ -171,7 +274,8 @@ lbm_status launch_one_step(lbm_sim* s, bool diag) {
     a.write_state = 1;
     a.want_diag = diag ? 1 : 0;
     a.hist = s->hist;
-    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    lbm_status st = launch_variant(s, s->var, a, s->cur);
+    if (st != LBM_OK) return st;
     s->cur = 1 - s->cur;
     return LBM_OK;
 }
@@ -189,10 +293,13 @@ lbm_status autotune(lbm_sim* s) {
     }
     int nv = n_variants(s->D);
     std::vector<int> vars;
-    if (s->opts.tile >= 0 && s->opts.tile < nv)
+    if (s->opts.tile >= 0 && (s->opts.tile < nv || tma_applicable(s, s->opts.tile))) {
         vars.push_back(s->opts.tile);
-    else
+    } else {
         for (int v = 0; v < nv; ++v) vars.push_back(v);
+        for (int k = 0; k < n_tma_variants(s->D); ++k)
+            if (tma_applicable(s, kTmaBase + k)) vars.push_back(kTmaBase + k);
+    }
     std::vector<int> chunks = s->opts.chunk > 0 ? std::vector<int>{s->opts.chunk} : chunk_candidates(s);
     if (vars.size() * chunks.size() == 1) {
         s->var = vars[0];
@@ -215,14 +322,16 @@ lbm_status autotune(lbm_sim* s) {
             a.want_diag = 0;
             size_t smem = step_smem(s->D, s->dtype, v);
             if (smem > 227 * 1024) continue;
-            cudaError_t e = launch_step(s->D, s->dtype, v, a, s->stream);
-            if (e != cudaSuccess) {
+            if (launch_variant(s, v, a, s->cur) != LBM_OK) {
                 cudaGetLastError();
                 continue;
             }
             const int reps = 3;
             CK(cudaEventRecord(e0, s->stream));
-            for (int r = 0; r < reps; ++r) CK(launch_step(s->D, s->dtype, v, a, s->stream));
+            for (int r = 0; r < reps; ++r) {
+                lbm_status st = launch_variant(s, v, a, s->cur);
+                if (st != LBM_OK) return st;
+            }
             CK(cudaEventRecord(e1, s->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
@@ -271,6 +380,7 @@ lbm_status check_flag(lbm_sim* s) {
     int h = 0;
     CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    if (h & 4) return fail(LBM_ETIMEOUT, "a bounded device-side wait for a tile copy gave up");
     if (h & 1) return fail(LBM_EUNSTABLE, "state became non-physical (rho <= 0 or not finite)");
     return LBM_OK;
 }
@@ -505,7 +615,8 @@ lbm_status lbm_moments(lbm_sim* s, lbm_fields_out* out) {
     a.write_state = 0;
     a.want_diag = 0;
     a.mout = s->fields;
-    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    st = launch_variant(s, s->var, a, s->cur);
+    if (st != LBM_OK) return st;
     const long long N = s->N;
     if (out->rho) CK(cudaMemcpyAsync(out->rho, s->fields, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     if (out->u)
@@ -528,7 +639,8 @@ lbm_status lbm_diagnostics(lbm_sim* s, double* out) {
     a.want_diag = 1;
     a.diag_out = s->diag_out;
     a.hist = nullptr;
-    CK(launch_step(s->D, s->dtype, s->var, a, s->stream));
+    st = launch_variant(s, s->var, a, s->cur);
+    if (st != LBM_OK) return st;
     CK(cudaMemcpyAsync(out, s->diag_out, (size_t)(s->D + 2) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return check_flag(s);

@@ -22,17 +22,47 @@ LBM_DECLARE_D(2)
 LBM_DECLARE_D(3)
 #undef LBM_DECLARE_D
 
+#define LBM_DECLARE_TMA(DD)                                                          \
+    int n_tma_variants_d##DD();                                                      \
+    Variant tma_variant_d##DD(int v);                                                \
+    cudaError_t tma_box_d##DD(int dtype, int v, TmaBox* box);                         \
+    cudaError_t launch_step_tma_d##DD(int dtype, int v, const TmaArgs& ta, cudaStream_t st);
+LBM_DECLARE_TMA(2)
+LBM_DECLARE_TMA(3)
+#undef LBM_DECLARE_TMA
+
 #define LBM_BY_D(D, call1, call2, call3, bad) \
     ((D) == 1 ? (call1) : (D) == 2 ? (call2) : (D) == 3 ? (call3) : (bad))
 
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
 
+int n_tma_variants(int D) { return D == 2 ? n_tma_variants_d2() : (D == 3 ? n_tma_variants_d3() : 0); }
+
 Variant variant(int D, int v) {
+    if (v >= kTmaBase) {
+        const int k = v - kTmaBase;
+        return D == 2 ? tma_variant_d2(k) : (D == 3 ? tma_variant_d3(k) : Variant{0, 0});
+    }
     return LBM_BY_D(D, variant_d1(v), variant_d2(v), variant_d3(v), (Variant{0, 0}));
 }
 
+cudaError_t tma_box(int D, int dtype, int v, TmaBox* box) {
+    const int k = v - kTmaBase;
+    return D == 2 ? tma_box_d2(dtype, k, box) : (D == 3 ? tma_box_d3(dtype, k, box) : cudaErrorInvalidValue);
+}
+
 size_t step_smem(int D, int dtype, int v) {
+    if (v >= kTmaBase) {
+        TmaBox b{};
+        return tma_box(D, dtype, v, &b) == cudaSuccess ? (size_t)b.smem : (size_t)0;
+    }
     return LBM_BY_D(D, step_smem_d1(dtype, v), step_smem_d2(dtype, v), step_smem_d3(dtype, v), (size_t)0);
+}
+
+cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
+    const int k = v - kTmaBase;
+    return D == 2 ? launch_step_tma_d2(dtype, k, ta, st)
+                  : (D == 3 ? launch_step_tma_d3(dtype, k, ta, st) : cudaErrorInvalidValue);
 }
 
 dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk) {

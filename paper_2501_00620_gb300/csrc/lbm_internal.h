@@ -1,10 +1,11 @@
-// Internal interface between the C-ABI runtime and the per-dimension kernel
-// launchers.  Not part of the public header.
+// Internal interface between the C-ABI runtime and the kernel launchers.
+// Not part of the public header.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include "lbm_step.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -14,15 +15,26 @@ struct Variant {
     int tx, ty;
 };
 
-// Kernel variants (tile shapes) available for a dimension.
+// Variant indices: 0..n_variants(D)-1 select the generic kernel's tiles;
+// kTmaBase + k selects the k-th tile of the TMA-staged kernel.
+constexpr int kTmaBase = 100;
+
+// Slice geometry of a TMA variant (for the host-side tensor maps).
+struct TmaBox {
+    int sxf, sxb, sy, pxf, smem;
+};
+
 int n_variants(int D);
+int n_tma_variants(int D);
 Variant variant(int D, int v);
 size_t step_smem(int D, int dtype, int v);
+cudaError_t tma_box(int D, int dtype, int v, TmaBox* box);
 
 // Grid of a step launch for extents and chunk.
 dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk);
 
 cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st);
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
                         void* b, long long N, cudaStream_t st);
 cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,

@@ -1,0 +1,68 @@
+// Launchers of the TMA-staged step kernel for the D2 lattice (tile shape and
+// prefetch depth per variant).
+#include "lbm_internal.h"
+#include "lbm_step_tma.cuh"
+
+namespace lbm {
+
+namespace {
+constexpr int kD = 2;
+constexpr Variant kTmaVariants[] = {{128, 1}, {128, 1}, {64, 1}, {64, 1}};
+constexpr int kNV = sizeof(kTmaVariants) / sizeof(kTmaVariants[0]);
+
+template <typename FS, int TX, int TY, int PF>
+cudaError_t launch_one(const TmaArgs& ta, cudaStream_t st) {
+    using Sh = TmaShape<kD, FS, TX, TY, PF>;
+    auto kern = step_tma_kernel<kD, FS, TX, TY, PF>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const StepArgs& a = ta.s;
+    const int np = kD == 3 ? a.nz : a.ny;
+    dim3 grid(a.nx / TX, kD == 3 ? a.ny / TY : 1, (np + a.chunk - 1) / a.chunk);
+    kern<<<grid, Sh::NT, Sh::SMEM, st>>>(ta);
+    return cudaGetLastError();
+}
+
+template <typename FS, int TX, int TY, int PF>
+void box_of(TmaBox* b) {
+    using Sh = TmaShape<kD, FS, TX, TY, PF>;
+    b->sxf = Sh::SXF;
+    b->sxb = Sh::SXB;
+    b->sy = Sh::SY;
+    b->pxf = Sh::PXF;
+    b->smem = Sh::SMEM;
+}
+
+template <typename FS>
+cudaError_t by_variant(int v, const TmaArgs* ta, TmaBox* box, cudaStream_t st) {
+    switch (v) {
+        case 0: if (box) { box_of<FS, 128, 1, 1>(box); return cudaSuccess; } return launch_one<FS, 128, 1, 1>(*ta, st);
+        case 1: if (box) { box_of<FS, 128, 1, 3>(box); return cudaSuccess; } return launch_one<FS, 128, 1, 3>(*ta, st);
+        case 2: if (box) { box_of<FS, 64, 1, 3>(box); return cudaSuccess; } return launch_one<FS, 64, 1, 3>(*ta, st);
+        case 3: if (box) { box_of<FS, 64, 1, 1>(box); return cudaSuccess; } return launch_one<FS, 64, 1, 1>(*ta, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t by_dtype(int dtype, int v, const TmaArgs* ta, TmaBox* box, cudaStream_t st) {
+    switch (dtype) {
+        case DT_F32: return by_variant<float>(v, ta, box, st);
+        case DT_F16: return by_variant<__half>(v, ta, box, st);
+        case DT_BF16: return by_variant<__nv_bfloat16>(v, ta, box, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+int n_tma_variants_d2() { return kNV; }
+Variant tma_variant_d2(int v) { return kTmaVariants[v]; }
+cudaError_t tma_box_d2(int dtype, int v, TmaBox* box) { return by_dtype(dtype, v, nullptr, box, nullptr); }
+cudaError_t launch_step_tma_d2(int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
+    return by_dtype(dtype, v, &ta, nullptr, st);
+}
+
+}  // namespace lbm

@@ -120,6 +120,10 @@ template <typename R> struct Equilibrium<2, R> {
     }
 };
 
+// Accumulators start at -0.0: x + (-0.0) == x for every x, so the compiler
+// may drop that add (it may not drop 0.0 + x, which differs for x = -0.0).
+// Products with compile-time zero velocity components are skipped for the
+// same reason (0 * x is not foldable under IEEE rules).
 template <typename R> struct Equilibrium<3, R> {
     __device__ __forceinline__ static void dev(R rho, const R* u, R* df) {
         using L = Lattice<3>;
@@ -129,14 +133,19 @@ template <typename R> struct Equilibrium<3, R> {
         df[0] = R(1.0 / 3.0) * (dr + rho * (R(-2.0 / 3.0) * S - R(2) * (X * Y + X * Z + Y * Z)));
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
-            const R eu = R(L::e(i, 0)) * u[0] + R(L::e(i, 1)) * u[1] + R(L::e(i, 2)) * u[2];
+            R eu = R(-0.0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (L::e(i, a) != 0) eu += R(L::e(i, a)) * u[a];
             const R eu2 = eu * eu;
             if (norm2<3>(i) == 1) {
                 const R p = R(3) * eu + R(4) * eu2 - R(2) * S + R(6) * eu2 * (S - eu2);
                 df[i] = R(1.0 / 18.0) * (dr + rho * p);
             } else {
-                const R q = R(L::e(i, 0) * L::e(i, 0)) * X + R(L::e(i, 1) * L::e(i, 1)) * Y +
-                            R(L::e(i, 2) * L::e(i, 2)) * Z;
+                R q = R(-0.0);
+                if (L::e(i, 0) != 0) q += X;
+                if (L::e(i, 1) != 0) q += Y;
+                if (L::e(i, 2) != 0) q += Z;
                 const R h = eu2 - q;
                 const R p = R(3) * eu + R(3) * eu2 - q - R(1.5) * h * h;
                 df[i] = R(1.0 / 36.0) * (dr + rho * p);
@@ -153,12 +162,13 @@ template <typename R> struct Equilibrium<3, R> {
 template <int D, typename R>
 __device__ __forceinline__ R forcing_term(int i, const R* F, const R* G, R trG) {
     using L = Lattice<D>;
-    R eF = R(0), eGe = R(0);
+    R eF = R(-0.0), eGe = R(-0.0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        eF += R(L::e(i, a)) * F[a];
+        if (L::e(i, a) != 0) eF += R(L::e(i, a)) * F[a];
 #pragma unroll
-        for (int b = 0; b < D; ++b) eGe += R(L::e(i, a) * L::e(i, b)) * G[sym<D>(a, b)];
+        for (int b = 0; b < D; ++b)
+            if (L::e(i, a) * L::e(i, b) != 0) eGe += R(L::e(i, a) * L::e(i, b)) * G[sym<D>(a, b)];
     }
     return R(L::w(i)) * (R(3) * eF + R(4.5) * eGe - R(1.5) * trG);
 }

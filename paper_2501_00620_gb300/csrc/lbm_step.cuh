@@ -1,67 +1,34 @@
 // Fused single-pass update of the bump-function lattice Boltzmann method
-// (arXiv 2501.00620, Sec. II.C), pull scheme with A-B buffers.
+// (arXiv 2501.00620, Sec. II.C), pull scheme with A-B buffers -- the generic
+// kernel (any extents, FP64 included; loads through the L1/L2 caches).
 //
 // Stored state: the EMITTED (post-collision, about-to-stream) populations
 // S_i(x) = fbar*_i(x) and variance bt*(x) of the last step.  One launch maps
 // S(t) -> S(t+1):
 //   stage 1 (every site of the tile plus a one-site ring):
 //     pull fbar_i(x) = S_i(x - e_i) (Eq. 49) and the mass-weighted variance
-//     bbar(x) = sum_i fbar_i bt*(x - e_i) / rho (Eq. 66); moments rho, j0,
-//     Ebar (Eqs. 56-57 before correction); rho*b for the gradient with b^eq at
-//     the uncorrected velocity (Eq. 68); u0 and rho*b go to shared memory.
-//   stage 2 (tile sites):
-//     F = -div(rho b) (Eq. 59), G = -div(rho u0 b + rho u0 b) (Eq. 61) by the
-//     lattice-weight central difference d_a phi = 3 sum_i w_i e_ia phi(x+e_i);
-//     u = (j0 + F/2)/rho (Eq. 57); T (isothermal T0 or thermal);
-//     fbar* = fbar + omega (f^eq + tau Phi - fbar) (Eq. 55);
-//     bbar* = bbar + omega (b^eq - bbar) (Eqs. 63, 65); store S(t+1).
+//     bbar(x) = sum_i fbar_i bt*(x - e_i) / rho (Eq. 66); moments; rho*b for
+//     the gradient (Eq. 68); u0 and rho*b go to shared memory.
+//   stage 2 (tile sites): gradient corrections, equilibrium + forcing, SRT
+//     update, store S(t+1) (site_collide).
 // The gradient needs rho*b on the neighbours, which exist only after the
-// neighbours have pulled; the ring is recomputed per tile (stage 1 on
-// (TX+2) x (TY+2) sites per plane) and the kernel marches along the slowest
-// axis keeping three planes of (u0, rho b) in a rolling shared-memory window,
-// so each stored value is read from HBM about once per step.
+// neighbours have pulled; the ring is recomputed per tile and the kernel
+// marches along the slowest axis keeping three planes of (u0, rho b) in a
+// rolling shared-memory window, so each stored value is read from HBM about
+// once per step.
 #pragma once
 
 #include <cstdint>
 
-#include "lbm_lattice.cuh"
+#include "lbm_site.cuh"
 
 namespace lbm {
-
-struct StepArgs {
-    const void* fin;      // Q planes, storage type: emitted df at t
-    const void* bin;      // NB planes, breal: emitted bt at t
-    void* fout;           // Q planes: emitted df at t+1 (write_state)
-    void* bout;           // NB planes
-    int nx, ny, nz;
-    int chunk;            // planes per block along the march axis
-    long long N;
-    double omega, tau, T0;
-    int thermal;
-    int fixed_x;          // 1: frozen reservoirs outside [0, nx)
-    long long rows;       // ny * nz (reservoir rows)
-    const void* gf;       // reservoirs, real: [2][Q][rows] df
-    const void* gb;       // [2][NB][rows] bt
-    const void* gaux;     // [2][D+NB][rows] u (D), rho*b (NB)
-    int write_state;      // 1: collide and store S(t+1)
-    double* mout;         // if non-null: rho (N), u (D*N), T (N) in FP64
-    int want_diag;        // 1: reduce mass, momentum, energy of the state at t
-    double* partial;      // [gridDim total][D+2] per-block sums
-    unsigned int* ticket; // completion counter for the last-block reduction
-    double* diag_out;     // if non-null: the D+2 global sums
-    double* hist;         // history ring: records of D+3 doubles
-    int hist_cap;
-    long long* step_ctr;  // device step counter (history index)
-    int* flag;            // bit 0: fatal (rho <= 0 or non-finite); bit 1: T <= 0 seen
-};
 
 __device__ __forceinline__ int wrap1(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 __device__ __forceinline__ int modp(int c, int n) {
     int r = c % n;
     return r < 0 ? r + n : r;
 }
-
-template <typename R> __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
 
 // Shared-memory footprint of the aux window: 3 planes x (D + NB) x region.
 template <int D, typename FS, int TX, int TY> struct StepShape {
@@ -83,7 +50,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     using real = typename Store<FS>::real;
     using breal = typename Store<FS>::breal;
     constexpr int Q = L::Q, NB = L::NB, NAUX = Sh::NAUX;
-    constexpr int RX = Sh::RX, RS = Sh::RS, NSLOT = Sh::NSLOT;
+    constexpr int RX = Sh::RX, RS = Sh::RS;
     constexpr int NT = TX * TY;
     constexpr int NRING = RS - TX * TY;
 
@@ -105,7 +72,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     const int p0 = (D == 1) ? 0 : blockIdx.z * a.chunk;
     const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np);
     const long long N = a.N;
-    const real omega = real(a.omega), tau = real(a.tau), T0 = real(a.T0);
+    const real omega = real(a.omega), T0 = real(a.T0);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     // interior site of this thread in region coordinates
@@ -141,8 +108,8 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
 
     auto slot_of = [&](int p) { return (D == 1) ? 0 : (p - p0 + 1) % 3; };
 
-    // Stage 1 for one region site.  (gx, gy, gz): unwrapped global coords.
-    // Writes u0, rho*b into aux[slot]; returns the site values if `keep`.
+    // Stage 1 for one region site at march plane q (wrapped).  Writes u0 and
+    // rho*b into aux[slot]; returns the site's values if `keep`.
     auto stage1_site = [&](int rx, int ry, int q, int slot, bool keep, real* o_df, real* o_bt,
                            real& o_rho, real* o_j, real& o_E) {
         int gx = x0 - 1 + rx;
@@ -159,11 +126,9 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
             return;
         }
         if (!a.fixed_x) gx = modp(gx, nx);
-        // pull
         real df[Q], bsum[NB];
-        real rho = real(0);
 #pragma unroll
-        for (int k = 0; k < NB; ++k) bsum[k] = real(0);
+        for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int sx = gx - L::e(i, 0);
@@ -186,49 +151,13 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
             }
             df[i] = v;
             const real fi = real(L::w(i)) + v;
-            rho += v;
 #pragma unroll
             for (int k = 0; k < NB; ++k) bsum[k] += fi * bv[k];
         }
-        rho += real(1);
-        const real irho = rcp(rho);
-        real j[D], bt[NB];
+        real bt[NB], rho, j[D], E, u0[D], rb[NB];
+        site_moments<D, real>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            j[c] = real(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if (L::e(i, c) != 0) j[c] += real(L::e(i, c)) * df[i];
-        }
-        real trb = real(0);
-#pragma unroll
-        for (int k = 0; k < NB; ++k) bt[k] = bsum[k] * irho;
-#pragma unroll
-        for (int c = 0; c < D; ++c) trb += bt[c];
-        // Ebar = sum fbar |e|^2 + rho tr bbar = sum df (|e|^2 - D/3) + rho tr bt
-        real E = rho * trb;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) E += real(norm2<D>(i) - D * (1.0 / 3.0)) * df[i];
-        real u0[D], uu = real(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            u0[c] = j[c] * irho;
-            uu += u0[c] * u0[c];
-        }
-        const real Tu = a.thermal ? (E - rho * uu) * irho * real(1.0 / D) : T0;
-        // rho*b for the gradient (Eq. 68): rho (bbar - (w/2)(bbar - b^eq(u0,Tu)))
-        // in shifted variables bt = b + I/3, bt^eq = T I + u u / 3.
-        const real hw = real(0.5) * omega;
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-            for (int d2 = c; d2 < D; ++d2) {
-                const int k = sym<D>(c, d2);
-                const real beq = u0[c] * u0[d2] * real(1.0 / 3.0) + (c == d2 ? Tu : real(0));
-                real rb = rho * (bt[k] - hw * (bt[k] - beq));
-                if (c == d2) rb -= rho * real(1.0 / 3.0);
-                aux[(slot * NAUX + D + k) * RS + r] = rb;
-            }
+        for (int k = 0; k < NB; ++k) aux[(slot * NAUX + D + k) * RS + r] = rb[k];
 #pragma unroll
         for (int c = 0; c < D; ++c) aux[(slot * NAUX + c) * RS + r] = u0[c];
         if (keep) {
@@ -246,10 +175,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     auto stage1 = [&](int q, bool keep_next) {
         const int qq = (D == 1) ? 0 : modp(q, np);
         const int slot = slot_of(q);
-        if (keep_next)
-            stage1_site(rxi, ryi, qq, slot, true, n_df, n_bt, n_rho, n_j, n_E);
-        else
-            stage1_site(rxi, ryi, qq, slot, false, n_df, n_bt, n_rho, n_j, n_E);
+        stage1_site(rxi, ryi, qq, slot, keep_next, n_df, n_bt, n_rho, n_j, n_E);
         if (tid < NRING) {
             real d_df[Q], d_bt[NB], d_rho, d_j[D], d_E;
             stage1_site(rxr, ryr, qq, slot, false, d_df, d_bt, d_rho, d_j, d_E);
@@ -263,12 +189,11 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
         const int gz = (D == 3) ? p : 0;
         if (gx >= nx || (D == 3 && gy >= ny)) return;
         const long long s = gx + (long long)nx * (gy + (long long)ny * gz);
-        // gradient terms
         real F[D], G[NB];
 #pragma unroll
-        for (int c = 0; c < D; ++c) F[c] = real(0);
+        for (int c = 0; c < D; ++c) F[c] = real(-0.0);
 #pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] = real(0);
+        for (int k = 0; k < NB; ++k) G[k] = real(-0.0);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int em = (D == 3) ? L::e(i, 2) : (D == 2 ? L::e(i, 1) : 0);
@@ -279,74 +204,13 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
             for (int k = 0; k < NB; ++k) rbn[k] = aux[(slot * NAUX + D + k) * RS + r];
 #pragma unroll
             for (int c = 0; c < D; ++c) un[c] = aux[(slot * NAUX + c) * RS + r];
-            real v[D];  // v_b = e_i . (rho b)_{., b}
-#pragma unroll
-            for (int b2 = 0; b2 < D; ++b2) {
-                v[b2] = real(0);
-#pragma unroll
-                for (int c = 0; c < D; ++c)
-                    if (L::e(i, c) != 0) v[b2] += real(L::e(i, c)) * rbn[sym<D>(c, b2)];
-            }
-            const real wi = real(L::w(i));
-#pragma unroll
-            for (int b2 = 0; b2 < D; ++b2) F[b2] += wi * v[b2];
-#pragma unroll
-            for (int b2 = 0; b2 < D; ++b2)
-#pragma unroll
-                for (int c = b2; c < D; ++c) G[sym<D>(b2, c)] += wi * (un[c] * v[b2] + un[b2] * v[c]);
+            fd_add<D, real>(i, rbn, un, F, G);
         }
 #pragma unroll
         for (int c = 0; c < D; ++c) F[c] *= real(-3);
 #pragma unroll
         for (int k = 0; k < NB; ++k) G[k] *= real(-3);
-        real trG = real(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) trG += G[c];
-        const real rho = c_rho, irho = rcp(rho);
-        real u[D], uu = real(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            u[c] = (c_j[c] + real(0.5) * F[c]) * irho;
-            uu += u[c] * u[c];
-        }
-        const real Ecorr = c_E + real(0.5) * trG;
-        const real Tm = (Ecorr - rho * uu) * irho * real(1.0 / D);
-        const real T = a.thermal ? Tm : T0;
-        // fatal: the method divides by rho; non-finite values propagate
-        if (!(rho > real(0)) || !isfinite(Ecorr) || !isfinite(uu)) bad |= 1;
-        // not fatal: a negative moment temperature only makes b^eq more
-        // negative (thermal mode); it occurs transiently at sharp fronts
-        if (a.thermal && !(Tm > real(0))) bad |= 2;
-        if (a.want_diag) {
-            acc[0] += double(rho);
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc[1 + c] += double(c_j[c]) + 0.5 * double(F[c]);
-            acc[D + 1] += double(Ecorr);
-        }
-        if (a.mout) {
-            a.mout[s] = double(rho);
-#pragma unroll
-            for (int c = 0; c < D; ++c) a.mout[(1 + c) * N + s] = double(u[c]);
-            a.mout[(1 + D) * N + s] = double(Tm);
-        }
-        if (!a.write_state) return;
-        real feq[Q];
-        Equilibrium<D, real>::dev(rho, u, feq);
-        FS* __restrict__ fout = static_cast<FS*>(a.fout);
-        breal* __restrict__ bout = static_cast<breal*>(a.bout);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const real tgt = feq[i] + tau * forcing_term<D, real>(i, F, G, trG);
-            Store<FS>::st(fout, (long long)i * N + s, c_df[i] + omega * (tgt - c_df[i]));
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-            for (int d2 = c; d2 < D; ++d2) {
-                const int k = sym<D>(c, d2);
-                const real beq = u[c] * u[d2] * real(1.0 / 3.0) + (c == d2 ? T : real(0));
-                bout[(long long)k * N + s] = breal(c_bt[k] + omega * (beq - c_bt[k]));
-            }
+        site_collide<D, FS, real>(a, s, c_df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     };
 
     auto carry = [&]() {
@@ -379,71 +243,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     }
 
     if (bad) atomicOr(a.flag, bad);
-
-    if (a.want_diag) {
-        // block reduction in a fixed order: warp shuffle, then warps in order
-        const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-        for (int k = 0; k < D + 2; ++k) {
-            double v = acc[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp * (D + 2) + k] = v;
-        }
-        __syncthreads();
-        const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-        __shared__ bool last;
-        if (tid == 0) {
-            for (int k = 0; k < D + 2; ++k) {
-                double v = 0.0;
-                for (int w = 0; w < NT / 32; ++w) v += red[w * (D + 2) + k];
-                a.partial[(long long)bid * (D + 2) + k] = v;
-            }
-            __threadfence();
-            last = (atomicAdd(a.ticket, 1u) == nblocks - 1);
-        }
-        __syncthreads();
-        if (last) {
-            // The last block sums the per-block partials: thread t takes
-            // blocks t, t + NT, ... in order, then the same fixed tree as
-            // above -- the result does not depend on block scheduling.
-            __threadfence();
-            double v[D + 2];
-#pragma unroll
-            for (int k = 0; k < D + 2; ++k) v[k] = 0.0;
-            for (unsigned int b2 = tid; b2 < nblocks; b2 += NT)
-#pragma unroll
-                for (int k = 0; k < D + 2; ++k) v[k] += __ldcg(a.partial + (long long)b2 * (D + 2) + k);
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < D + 2; ++k) {
-                double x = v[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0) red[warp * (D + 2) + k] = x;
-            }
-            __syncthreads();
-            double tot = 0.0;
-            if (tid < D + 2)
-                for (int w = 0; w < NT / 32; ++w) tot += red[w * (D + 2) + tid];
-            __syncthreads();
-            if (tid < D + 2) red[tid] = tot;
-            __syncthreads();
-            if (tid == 0) {
-                const long long st = *a.step_ctr;
-                if (a.diag_out)
-                    for (int k = 0; k < D + 2; ++k) a.diag_out[k] = red[k];
-                if (a.hist) {
-                    double* rec = a.hist + (st % a.hist_cap) * (D + 3);
-                    rec[0] = double(st);
-                    for (int k = 0; k < D + 2; ++k) rec[1 + k] = red[k];
-                }
-                if (a.write_state) *a.step_ctr = st + 1;
-                *a.ticket = 0u;
-            }
-        }
-    }
+    if (a.want_diag) block_diagnostics<D, NT>(a, acc, red);
 }
 
 // ---------------------------------------------------------------------------

@@ -245,3 +245,30 @@ def test_fixed_state_uniform_is_steady():
     s.step(20)
     r, u, T = s.moments()
     assert abs(r - 1).max() < 1e-14 and abs(u).max() < 1e-14 and abs(T - 0.12).max() < 1e-14
+
+
+def test_riemann_amplifies_rounding():
+    """Config 2 is ill-conditioned in the oracle itself: rounding-sized noise
+    (relative 1e-12 on the emitted populations, every step -- the way two
+    different roundings differ) grows ~100x per 500 steps while the shock is
+    in the domain, and the difference peaks at the shock."""
+    Tu = W.T_UNIT_RIEMANN
+    rho, u, T = W.riemann_1d(4096, Tu)
+    a = oracle.Sim(1, 4096, tau=0.55, T0=Tu, thermal=True, bc="fixed")
+    b = oracle.Sim(1, 4096, tau=0.55, T0=Tu, thermal=True, bc="fixed")
+    a.init(rho, u, T)
+    b.init(rho, u, T)
+    rng = np.random.default_rng(1)
+    diff = {}
+    for t in range(1, 1501):
+        a.step(1)
+        b.step(1)
+        f, bb = b.emitted()
+        b.set_emitted(f * (1 + 1e-12 * rng.standard_normal(f.shape)), bb)
+        if t in (500, 1500):
+            ra, _, _ = a.moments()
+            rb, _, _ = b.moments()
+            diff[t] = np.abs(ra - rb)[0, 0]
+    assert diff[1500].max() > 1e3 * diff[500].max()
+    x_shock = 2048 + 0.88 * 1500
+    assert abs(int(np.argmax(diff[1500])) - x_shock) < 50
