@@ -193,6 +193,47 @@ long lbm_step_count(const lbm_sim *sim);
 lbm_status lbm_save(lbm_sim *sim, const char *path);
 lbm_status lbm_load(lbm_sim *sim, const char *path);
 
+/* One time step that allocates no device memory, on device buffers the
+ * caller owns.  The paper has no counterpart: this is a library service for
+ * callers that may not allocate device memory while they run, such as
+ * real-time loops that cannot take the synchronisation an allocator may
+ * impose, or host frameworks and plugins that own every device allocation
+ * and give a library none.  Such a caller allocates the state once, up front,
+ * and advances it with this call.
+ *
+ * It runs the same fused step as lbm_step (periodic boundary in every
+ * direction, FP64 storage) on the emitted state, in the kernel's own layout:
+ *   f_in, f_out: Q planes of N doubles, plane i = fbar*_i - w_i
+ *                (the emitted population minus its lattice weight);
+ *   b_in, b_out: nb planes of N doubles, bbar* + I/3 (the diagonal planes
+ *                shifted by 1/3, the off-diagonal planes unchanged);
+ * with the plane and site order of lbm_get_state.  f_in/b_in hold the state
+ * at step t, f_out/b_out receive step t+1; input and output must not overlap.
+ * diag_out (device pointer or NULL) receives dim+2 doubles: mass, momentum
+ * and energy of the state at step t, as lbm_diagnostics gives them.
+ * tau, T0 and thermal are those of lbm_create_ex; stream is a cudaStream_t
+ * (NULL = legacy default stream).  The call is blocking: it waits for the
+ * step on `stream` and returns LBM_EUNSTABLE if the new state is
+ * non-physical (rho <= 0 or not finite).
+ *
+ * Scratch: the per-block partial sums of the diagnostics, the reduction's
+ * completion ticket and the status flag live in one fixed 1 MiB device
+ * array inside the library (present on every GPU the library is loaded on),
+ * so the lattice may span at most (2^20 - 256) / (8 (dim+2)) thread blocks:
+ * 43,680 in 1D (256 sites each, 11.1 M sites), 32,760 in 2D (128 x 64 sites
+ * each, 268 M sites), 26,208 in 3D (32 x 8 x 64 sites each, 429 M sites).
+ * A larger lattice is rejected with LBM_EINVAL and a message.  The call sets
+ * the ticket and flag to zero on `stream` before each launch; the partial
+ * sums need no clearing.  The first call on a device (with that device
+ * current) looks up the array's device address with cudaGetSymbolAddress and
+ * sets the kernels' shared-memory attribute; make that first call before
+ * any stream capture.  The array is shared by all calls on one device, so
+ * two calls that overlap in time on one device -- from two host threads, or
+ * on two streams -- race on it and may return wrong diagnostics or flags. */
+lbm_status lbm_step_noalloc(int dim, int nx, int ny, int nz, double tau, double T0, int thermal,
+                            const double *f_in, const double *b_in, double *f_out, double *b_out,
+                            double *diag_out, void *stream);
+
 /* Free all device memory of the simulation. */
 void lbm_destroy(lbm_sim *sim);
 

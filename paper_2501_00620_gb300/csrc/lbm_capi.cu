@@ -50,6 +50,12 @@ const int kHistCap = 4096;
 
 }  // namespace
 
+namespace lbm {
+// Error message of the calling thread for lbm_last_error(), set by entry
+// points implemented in other translation units.
+void set_last_error(const std::string& m) { g_err = m; }
+}  // namespace lbm
+
 struct lbm_sim {
     int D = 0, Q = 0, NB = 0;
     int nx = 1, ny = 1, nz = 1;

@@ -91,13 +91,14 @@ def _load():
     L.lbm_step_count.restype = ctypes.c_long
     L.lbm_save.argtypes = [vp, ctypes.c_char_p]
     L.lbm_load.argtypes = [vp, ctypes.c_char_p]
+    L.lbm_step_noalloc.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int] + [vp] * 6
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
-                 "lbm_save", "lbm_load"):
+                 "lbm_save", "lbm_load", "lbm_step_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -195,6 +196,14 @@ def lbm_save(sim, path):
 
 def lbm_load(sim, path):
     _check(_lib.lbm_load(sim, os.fsencode(path)))
+
+
+def lbm_step_noalloc(dim, nx, ny, nz, tau, T0, thermal, f_in, b_in, f_out, b_out, diag_out=None, stream=None):
+    """One step on caller-owned FP64 device buffers without any device
+    allocation (the library's fixed scratch array); pointers are integers
+    (e.g. ``tensor.data_ptr()``), ``diag_out`` and ``stream`` may be None."""
+    _check(_lib.lbm_step_noalloc(dim, nx, ny, nz, float(tau), float(T0), int(bool(thermal)),
+                                 f_in, b_in, f_out, b_out, diag_out, stream))
 
 
 def lbm_destroy(sim):

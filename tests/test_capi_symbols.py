@@ -55,3 +55,27 @@ def test_argument_validation_needs_no_gpu(lib):
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_create(*args, bc=lbm.LBM_BC_PERIODIC)
         assert e.value.status == lbm.LBM_EINVAL
+
+
+def test_noalloc_step_rejects_before_any_cuda_call(lib):
+    """The no-allocation step validates its sizes on the host first: a lattice
+    needing more diagnostics scratch than the fixed array holds is refused
+    with a message, before the buffers are touched."""
+    from paper_2501_00620_gb300 import lbm
+    buf = [16 * (k + 1) for k in range(4)]  # placeholders, never dereferenced on these paths
+    cases = [
+        ((0, 8, 1, 1, 0.8, 0.3, 0), "extents"),
+        ((2, 8, 8, 2, 0.8, 0.3, 0), "extents"),
+        ((2, 8, 8, 1, 0.0, 0.3, 0), "tau"),
+        ((1, 43681 * 256, 1, 1, 0.8, 0.3, 0), "too large"),
+        ((2, 128 * 182, 64 * 181, 1, 0.8, 0.3, 0), "too large"),
+        ((3, 32 * 100, 8 * 100, 64 * 3, 0.52, 0.05, 0), "too large"),
+    ]
+    for args, msg in cases:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_step_noalloc(*args, *buf)
+        assert e.value.status == lbm.LBM_EINVAL
+        assert msg in str(e.value)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_step_noalloc(1, 8, 1, 1, 0.8, 0.3, 0, buf[0], buf[1], buf[0], buf[3])
+    assert "differ" in str(e.value)
