@@ -185,6 +185,15 @@ lbm_status lbm_flags(lbm_sim *sim, int *flags);
 /* Number of steps taken since lbm_init. */
 long lbm_step_count(const lbm_sim *sim);
 
+/* The launch configuration of the step (library service, no counterpart in
+ * the paper): *tile = the tile variant in use (0.. the generic fused kernel,
+ * 100.. the shared-memory-staged kernels), *chunk = planes per thread block
+ * along the slowest axis, *kernel = name of the kernel template (static
+ * string).  Fixed by opts.tile/opts.chunk or by the autotuner at the first
+ * lbm_step; before that *tile = *chunk = -1 and *kernel = "".  Any pointer
+ * may be NULL.  Host only, never fails for a valid handle. */
+lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const char **kernel);
+
 /* Checkpoint: write / read the full state (emitted planes in the storage
  * dtype, reservoirs, step counter, parameters) as a raw file with a small
  * header.  lbm_load requires a simulation created with the same dim, extents,

@@ -174,6 +174,8 @@ bool tma_applicable(const lbm_sim* s, int v) {
     if (s->nx < 2 || (s->D == 3 && s->ny < 2)) return false;
     // the march index wraps with one conditional add or subtract
     if ((s->D == 3 ? s->nz : s->ny) < 4) return false;
+    // site indices are 32-bit in the staged kernels
+    if (s->N >= (1LL << 31)) return false;
     return encode_fn() != nullptr;
 }
 
@@ -601,6 +603,14 @@ lbm_status lbm_sync(lbm_sim* s) {
 }
 
 long lbm_step_count(const lbm_sim* s) { return s ? s->nstep : -1; }
+
+lbm_status lbm_launch_config(const lbm_sim* s, int* tile, int* chunk, const char** kernel) {
+    if (!s) return fail(LBM_EINVAL, "NULL simulation");
+    if (tile) *tile = s->var;
+    if (chunk) *chunk = s->var >= 0 ? s->chunk : -1;
+    if (kernel) *kernel = s->var >= 0 ? kernel_name(s->D, s->var) : "";
+    return LBM_OK;
+}
 
 lbm_status lbm_flags(lbm_sim* s, int* flags) {
     if (!s || !flags) return fail(LBM_EINVAL, "NULL argument");

@@ -1,5 +1,6 @@
 // Dimension dispatch for the kernel launchers.
 #include "lbm_internal.h"
+#include "lbm_fast_launch.cuh"
 
 namespace lbm {
 
@@ -35,6 +36,12 @@ LBM_DECLARE_TMA(3)
     ((D) == 1 ? (call1) : (D) == 2 ? (call2) : (D) == 3 ? (call3) : (bad))
 
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
+
+const char* kernel_name(int D, int v) {
+    if (v < kTmaBase) return "step_kernel";
+    const int nfast = D == 2 ? n_fast_variants_d2() : (D == 3 ? n_fast_variants_d3() : 0);
+    return v - kTmaBase >= n_tma_variants(D) - nfast ? "step_fast_kernel" : "step_tma_kernel";
+}
 
 int n_tma_variants(int D) { return D == 2 ? n_tma_variants_d2() : (D == 3 ? n_tma_variants_d3() : 0); }
 

@@ -25,6 +25,8 @@ struct TmaBox {
 };
 
 int n_variants(int D);
+// Name of the kernel template variant v launches (for reports).
+const char* kernel_name(int D, int v);
 int n_tma_variants(int D);
 Variant variant(int D, int v);
 size_t step_smem(int D, int dtype, int v);

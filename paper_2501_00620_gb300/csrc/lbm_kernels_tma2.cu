@@ -1,6 +1,7 @@
 // Launchers of the TMA-staged step kernel for the D2 lattice (tile shape and
 // prefetch depth per variant).
 #include "lbm_internal.h"
+#include "lbm_fast_launch.cuh"
 #include "lbm_step_tma.cuh"
 
 namespace lbm {
@@ -58,11 +59,15 @@ cudaError_t by_dtype(int dtype, int v, const TmaArgs* ta, TmaBox* box, cudaStrea
 }
 }  // namespace
 
-int n_tma_variants_d2() { return kNV; }
-Variant tma_variant_d2(int v) { return kTmaVariants[v]; }
-cudaError_t tma_box_d2(int dtype, int v, TmaBox* box) { return by_dtype(dtype, v, nullptr, box, nullptr); }
+// Indices past this file's table select the occupancy-oriented kernel
+// (lbm_kernels_fast2.cu).
+int n_tma_variants_d2() { return kNV + n_fast_variants_d2(); }
+Variant tma_variant_d2(int v) { return v < kNV ? kTmaVariants[v] : fast_variant_d2(v - kNV); }
+cudaError_t tma_box_d2(int dtype, int v, TmaBox* box) {
+    return v < kNV ? by_dtype(dtype, v, nullptr, box, nullptr) : fast_box_d2(dtype, v - kNV, box);
+}
 cudaError_t launch_step_tma_d2(int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
-    return by_dtype(dtype, v, &ta, nullptr, st);
+    return v < kNV ? by_dtype(dtype, v, &ta, nullptr, st) : launch_step_fast_d2(dtype, v - kNV, ta, st);
 }
 
 }  // namespace lbm

@@ -65,6 +65,15 @@ template <int D> __host__ __device__ constexpr int norm2(int i) {
            Lattice<D>::e(i, 2) * Lattice<D>::e(i, 2);
 }
 
+// Index of the velocity -e_i.
+template <int D> __host__ __device__ constexpr int opposite(int i) {
+    using L = Lattice<D>;
+    int r = -1;
+    for (int k = 0; k < L::Q; ++k)
+        if (L::e(k, 0) == -L::e(i, 0) && L::e(k, 1) == -L::e(i, 1) && L::e(k, 2) == -L::e(i, 2)) r = k;
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Equilibrium deviations df^eq_i = f^eq_i(rho, u) - w_i.
 //
@@ -153,25 +162,6 @@ template <typename R> struct Equilibrium<3, R> {
         }
     }
 };
-
-// ---------------------------------------------------------------------------
-// Forcing (Eqs. 58-61): Phi_i = w_i [ e_i.F / cs2 + (e_i e_i - cs2 I):G / (2 cs2^2) ]
-// with cs2 = 1/3, i.e. w_i [3 e.F + 9/2 e.G.e - 3/2 tr G].  Its zeroth, first
-// and second moments are 0, F and G on all three lattices (fourth-order
-// isotropy of the weights).
-template <int D, typename R>
-__device__ __forceinline__ R forcing_term(int i, const R* F, const R* G, R trG) {
-    using L = Lattice<D>;
-    R eF = R(-0.0), eGe = R(-0.0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        if (L::e(i, a) != 0) eF += R(L::e(i, a)) * F[a];
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-            if (L::e(i, a) * L::e(i, b) != 0) eGe += R(L::e(i, a) * L::e(i, b)) * G[sym<D>(a, b)];
-    }
-    return R(L::w(i)) * (R(3) * eF + R(4.5) * eGe - R(1.5) * trG);
-}
 
 // ---------------------------------------------------------------------------
 // Storage codecs.  Populations are stored as df = fbar* - w_i in the storage

@@ -11,6 +11,41 @@
 
 namespace lbm {
 
+// Per-thread accumulator of the conservation diagnostics (mass, momentum,
+// energy; K = D + 2 values).  In FP64 arithmetic it is a plain sum.  In FP32
+// arithmetic each value is a float-float pair (hi, lo) updated by the
+// error-free TwoSum transformation (Knuth, TAOCP vol. 2, 4.2.2): the pair
+// carries the exact sum of its inputs to about 2^-48 relative, as an FP64 sum
+// would, while costing only FP32 instructions (GB300's FP64 rate is a small
+// fraction of its FP32 rate).
+template <typename R, int K> struct DiagAcc;
+
+template <int K> struct DiagAcc<double, K> {
+    double v[K];
+    __device__ __forceinline__ DiagAcc() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = 0.0;
+    }
+    __device__ __forceinline__ void add(int k, double x) { v[k] += x; }
+    __device__ __forceinline__ double get(int k) const { return v[k]; }
+};
+
+template <int K> struct DiagAcc<float, K> {
+    float hi[K], lo[K];
+    __device__ __forceinline__ DiagAcc() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) hi[k] = lo[k] = 0.0f;
+    }
+    __device__ __forceinline__ void add(int k, float x) {
+        const float s = __fadd_rn(hi[k], x);
+        const float bp = __fsub_rn(s, hi[k]);
+        const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi[k] = s;
+        lo[k] = __fadd_rn(lo[k], err);
+    }
+    __device__ __forceinline__ double get(int k) const { return double(hi[k]) + double(lo[k]); }
+};
+
 // 1/x, correctly rounded (the same value as 1/x by IEEE division, in fewer
 // instructions than the division sequence).
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
@@ -27,17 +62,27 @@ __device__ __forceinline__ void site_moments(const R* df, const R* bsum, R omega
                                              R& rho, R* j, R& E, R* u0, R* rb) {
     using L = Lattice<D>;
     constexpr int Q = L::Q, NB = L::NB;
-    R r = R(-0.0);
+    // velocity pairs (e_i, -e_i): sums for the even moments, differences for
+    // the odd ones
+    R ps[Q], pd[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) r += df[i];
+    for (int i = 1; i < Q; ++i) {
+        if (i > opposite<D>(i)) continue;
+        ps[i] = df[i] + df[opposite<D>(i)];
+        pd[i] = df[i] - df[opposite<D>(i)];
+    }
+    R r = df[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if (i < opposite<D>(i)) r += ps[i];
     rho = r + R(1);
     const R irho = recip(rho);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         R acc = R(-0.0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            if (L::e(i, c) != 0) acc += R(L::e(i, c)) * df[i];
+        for (int i = 1; i < Q; ++i)
+            if (i < opposite<D>(i) && L::e(i, c) != 0) acc += R(L::e(i, c)) * pd[i];
         j[c] = acc;
     }
     R trb = R(-0.0);
@@ -45,9 +90,18 @@ __device__ __forceinline__ void site_moments(const R* df, const R* bsum, R omega
     for (int k = 0; k < NB; ++k) bt[k] = bsum[k] * irho;
 #pragma unroll
     for (int c = 0; c < D; ++c) trb += bt[c];
-    R e = rho * trb;
+    // sum_i df_i (|e_i|^2 - D/3): coefficient 0 (D3Q19 axis pairs) skipped
+    R e = rho * trb + R(-D * (1.0 / 3.0)) * df[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) e += R(norm2<D>(i) - D * (1.0 / 3.0)) * df[i];
+    for (int i = 1; i < Q; ++i) {
+        if (i > opposite<D>(i)) continue;
+        constexpr double third = 1.0 / 3.0;
+        const double coef = norm2<D>(i) - D * third;
+        if (coef == 1.0)
+            e += ps[i];
+        else if (coef != 0.0)
+            e += R(coef) * ps[i];
+    }
     E = e;
     R uu = R(-0.0);
 #pragma unroll
@@ -102,6 +156,91 @@ __device__ __forceinline__ void fd_add(int i, const R* rbn, const R* un, R* F, R
         }
 }
 
+// BGK update and store of the populations, pair by pair.  For a velocity pair
+// (e_i, -e_i) the target f^eq_i + tau Phi_i (Appendix A, Eqs. 55, 58-61)
+// splits into a part even in e_i, shared by the pair, and the odd part
+// 3 w_i e_i.(rho u + tau F) -- the first moments of the equilibrium and of
+// the forcing -- so that
+//   df*_(+/-) = (1 - omega) df_(+/-) + omega (even +/- odd).
+// Even parts (deviations from w_i, with dr = rho - 1, X_a = u_a^2):
+//   D3Q19 (Appendix A):  rest  (1/3)[dr + rho(-(2/3)S - 2(XY+XZ+YZ))]
+//                        axis  (1/18)[dr + rho(X_a(4 + 6(S - X_a)) - 2S)]
+//                        edge  (1/36)[dr + rho(3 eu^2 - X_a - X_b - 6 X_a X_b)]
+//   D2Q9, D1Q3: the even halves of the tensor-product moment inversion.
+// The forcing Phi_i = w_i [3 e_i.F + 9/2 e_i.G.e_i - 3/2 tr G] -- the
+// second-order Hermite projection whose zeroth, first and second moments are
+// 0, F and G (Eqs. 58-61) -- adds w_i tau (9/2 e_i.G.e_i - 3/2 tr G) to the
+// even part and 3 w_i tau e_i.F to the odd part.
+template <int D, typename FS, typename R>
+__device__ __forceinline__ void collide_store(FS* __restrict__ fo, long long N, const R* df, R rho, const R* u,
+                                              const R* F, const R* G, R trG, R omega, R tau) {
+    using L = Lattice<D>;
+    constexpr int Q = L::Q, NB = L::NB;
+    const R dr = rho - R(1);
+    const R om1 = R(1) - omega;
+    R mom[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) mom[c] = fma(tau, F[c], rho * u[c]);
+    const R F0 = R(-1.5) * tau * trG;
+    const R t45 = R(4.5) * tau;
+    R g45[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) g45[k] = t45 * G[k];
+    R ev[Q];  // even part of the target, at the rest population and the first member of each pair
+    if constexpr (D == 3) {
+        const R X0 = u[0] * u[0], X1 = u[1] * u[1], X2 = u[2] * u[2];
+        const R X[3] = {X0, X1, X2};
+        const R S = X0 + X1 + X2;
+        const R C0 = dr + F0;
+        ev[0] = R(1.0 / 3.0) * (C0 + rho * (R(-2.0 / 3.0) * S - R(2) * (X0 * X1 + X0 * X2 + X1 * X2)));
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (i > opposite<3>(i)) continue;
+            if (norm2<3>(i) == 1) {
+                const int a = L::e(i, 0) != 0 ? 0 : (L::e(i, 1) != 0 ? 1 : 2);
+                ev[i] = R(1.0 / 18.0) * (C0 + rho * (X[a] * (R(4) + R(6) * (S - X[a])) - R(2) * S) + g45[a]);
+            } else {
+                const int a = L::e(i, 0) != 0 ? 0 : 1;
+                const int b = L::e(i, 2) != 0 ? 2 : 1;
+                const int sab = L::e(i, a) * L::e(i, b);
+                const R eu = sab > 0 ? u[a] + u[b] : u[a] - u[b];
+                const R gab = sab > 0 ? g45[sym<3>(a, b)] : -g45[sym<3>(a, b)];
+                ev[i] = R(1.0 / 36.0) *
+                        (C0 + rho * (R(3) * eu * eu - X[a] - X[b] - R(6) * X[a] * X[b]) + (g45[a] + g45[b] + R(2) * gab));
+            }
+        }
+    } else if constexpr (D == 2) {
+        const R X = u[0] * u[0], Y = u[1] * u[1];
+        const R m20 = (dr + R(2) * rho * X) * R(1.0 / 3.0);
+        const R m02 = (dr + R(2) * rho * Y) * R(1.0 / 3.0);
+        const R m11 = R(2.0 / 3.0) * rho * u[0] * u[1];
+        const R m22 = (dr + rho * (R(2) * (X + Y) - R(6) * X * Y)) * R(1.0 / 9.0);
+        ev[0] = (dr - m20) - (m02 - m22) + R(4.0 / 9.0) * F0;
+        ev[1] = R(0.5) * (m20 - m22) + R(1.0 / 9.0) * (F0 + g45[0]);
+        ev[2] = R(0.5) * (m02 - m22) + R(1.0 / 9.0) * (F0 + g45[1]);
+        ev[5] = R(0.25) * (m22 + m11) + R(1.0 / 36.0) * (F0 + g45[0] + g45[1] + R(2) * g45[2]);
+        ev[6] = R(0.25) * (m22 - m11) + R(1.0 / 36.0) * (F0 + g45[0] + g45[1] - R(2) * g45[2]);
+    } else {
+        const R dm2 = (dr + R(2) * rho * u[0] * u[0]) * R(1.0 / 3.0);
+        ev[0] = dr - dm2 + R(2.0 / 3.0) * F0;
+        ev[1] = R(0.5) * dm2 + R(1.0 / 6.0) * (F0 + g45[0]);
+    }
+    Store<FS>::st(fo, 0, fma(om1, df[0], omega * ev[0]));
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int ib = opposite<D>(i);
+        if (i > ib) continue;
+        R eM = R(-0.0);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (L::e(i, c) != 0) eM += R(L::e(i, c)) * mom[c];
+        const R A = omega * ev[i];
+        const R B = (R(3.0 * L::w(i)) * omega) * eM;
+        Store<FS>::st(fo, i * N, fma(om1, df[i], A + B));
+        Store<FS>::st(fo, ib * N, fma(om1, df[ib], A - B));
+    }
+}
+
 // Stage 2 at one site, given F and G (already scaled): corrected velocity
 // u = (j0 + F/2)/rho (Eq. 57), temperature, diagnostics, the SRT update
 // fbar* = fbar + omega (f^eq + tau Phi - fbar) (Eq. 55, Appendix A, Eqs. 58-61)
@@ -109,11 +248,10 @@ __device__ __forceinline__ void fd_add(int i, const R* rbn, const R* un, R* F, R
 // bad |= 1: rho <= 0 or non-finite; bad |= 2: T <= 0 in thermal mode.
 template <int D, typename FS, typename R>
 __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, const R* c_df, const R* c_bt, R rho,
-                                             const R* c_j, R c_E, const R* F, const R* G, double* acc,
+                                             const R* c_j, R c_E, const R* F, const R* G, DiagAcc<R, D + 2>& acc,
                                              int& bad) {
     using L = Lattice<D>;
     using breal = typename Store<FS>::breal;
-    constexpr int Q = L::Q;
     const long long N = a.N;
     const R omega = R(a.omega), tau = R(a.tau), T0 = R(a.T0);
     R trG = R(-0.0);
@@ -135,10 +273,13 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
     // negative (thermal mode); it occurs transiently at sharp fronts
     if (a.thermal && !(Tm > R(0))) bad |= 2;
     if (a.want_diag) {
-        acc[0] += double(rho);
+        acc.add(0, rho);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[1 + c] += double(c_j[c]) + 0.5 * double(F[c]);
-        acc[D + 1] += double(Ecorr);
+        for (int c = 0; c < D; ++c) {
+            acc.add(1 + c, c_j[c]);
+            acc.add(1 + c, R(0.5) * F[c]);  // exact halving
+        }
+        acc.add(D + 1, Ecorr);
     }
     if (a.mout) {
         a.mout[s] = double(rho);
@@ -147,17 +288,8 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
         a.mout[(1 + D) * N + s] = double(Tm);
     }
     if (!a.write_state) return;
-    R feq[Q];
-    Equilibrium<D, R>::dev(rho, u, feq);
-    // plane-strided stores from one running pointer per array
-    FS* __restrict__ fo = static_cast<FS*>(a.fout) + s;
+    collide_store<D, FS, R>(static_cast<FS*>(a.fout) + s, N, c_df, rho, u, F, G, trG, omega, tau);
     breal* __restrict__ bo = static_cast<breal*>(a.bout) + s;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R tgt = feq[i] + tau * forcing_term<D, R>(i, F, G, trG);
-        Store<FS>::st(fo, 0, c_df[i] + omega * (tgt - c_df[i]));
-        fo += N;
-    }
     R bnew[L::NB];
 #pragma unroll
     for (int c = 0; c < D; ++c)
@@ -178,13 +310,13 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
 // then warps in order), per-block partials, and the last block's fixed-order
 // sum of all partials into the history record / diag_out.  `red` holds
 // 32 * (D + 2) doubles of shared memory.
-template <int D, int NT>
-__device__ __forceinline__ void block_diagnostics(const StepArgs& a, double* acc, double* red) {
+template <int D, int NT, typename R>
+__device__ __forceinline__ void block_diagnostics(const StepArgs& a, const DiagAcc<R, D + 2>& acc, double* red) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < D + 2; ++k) {
-        double v = acc[k];
+        double v = acc.get(k);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp * (D + 2) + k] = v;

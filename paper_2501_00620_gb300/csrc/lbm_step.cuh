@@ -43,8 +43,10 @@ template <int D, typename FS, int TX, int TY> struct StepShape {
     static constexpr size_t smem = aux_bytes + sizeof(double) * 32 * (D + 2);
 };
 
+// One tile (bx, by) x chunk bz of the fused step; the body of step_kernel,
+// also run per work item by the batched serving kernel.
 template <int D, typename FS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
+__device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, int bz, unsigned char* smem_raw) {
     using L = Lattice<D>;
     using Sh = StepShape<D, FS, TX, TY>;
     using real = typename Store<FS>::real;
@@ -54,7 +56,6 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     constexpr int NT = TX * TY;
     constexpr int NRING = RS - TX * TY;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     real* aux = reinterpret_cast<real*>(smem_raw);  // [NSLOT][NAUX][RS]
     double* red = reinterpret_cast<double*>(smem_raw + Sh::aux_bytes);
 
@@ -66,10 +67,10 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = (D == 3) ? blockIdx.y * TY : 0;
+    const int x0 = bx * TX;
+    const int y0 = (D == 3) ? by * TY : 0;
     const int np = (D == 3) ? a.nz : (D == 2 ? a.ny : 1);
-    const int p0 = (D == 1) ? 0 : blockIdx.z * a.chunk;
+    const int p0 = (D == 1) ? 0 : bz * a.chunk;
     const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np);
     const long long N = a.N;
     const real omega = real(a.omega), T0 = real(a.T0);
@@ -101,9 +102,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     real c_df[Q], c_bt[NB], c_rho, c_j[D], c_E;
     real n_df[Q], n_bt[NB], n_rho, n_j[D], n_E;
 
-    double acc[D + 2];
-#pragma unroll
-    for (int k = 0; k < D + 2; ++k) acc[k] = 0.0;
+    DiagAcc<real, D + 2> acc;
     int bad = 0;
 
     auto slot_of = [&](int p) { return (D == 1) ? 0 : (p - p0 + 1) % 3; };
@@ -244,6 +243,12 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
 
     if (bad) atomicOr(a.flag, bad);
     if (a.want_diag) block_diagnostics<D, NT>(a, acc, red);
+}
+
+template <int D, typename FS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_block<D, FS, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

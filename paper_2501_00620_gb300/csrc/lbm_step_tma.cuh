@@ -31,8 +31,6 @@
 
 namespace lbm {
 
-__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
-
 template <int D, typename FS, int TX, int TY, int PF> struct TmaShape {
     using L = Lattice<D>;
     static constexpr int Q = L::Q, NB = L::NB, NAUX = D + NB;
@@ -75,8 +73,6 @@ template <int D, typename FS, int TX, int TY, int PF> struct TmaShape {
     static_assert(NT <= 1024, "too many threads");
 };
 
-constexpr uint64_t kWaitLimit = 20000000ull;  // ns before a wait for a tile copy gives up
-
 // Per-block state of the march; every method is force-inlined so that the
 // carried site values stay in registers.
 template <int D, typename FS, int TX, int TY, int PF> struct TmaBlock {
@@ -94,10 +90,9 @@ template <int D, typename FS, int TX, int TY, int PF> struct TmaBlock {
     int tid, x0, y0, nx, ny, np, p0, p1;
     bool xlo, xhi, ylo, yhi, edge;
     uint32_t pphase = 0, bphase = 0, p_pending = 0, b_pending = 0;
-    int* abort_flag;
+    bool timed_out = false;  // a wait of this thread gave up
 
-    __device__ __forceinline__ TmaBlock(const TmaArgs& t, unsigned char* sm, int* ab)
-        : ta(t), a(t.s), smem(sm), abort_flag(ab) {
+    __device__ __forceinline__ TmaBlock(const TmaArgs& t, unsigned char* sm) : ta(t), a(t.s), smem(sm) {
         tid = threadIdx.x;
         x0 = blockIdx.x * TX;
         y0 = (D == 3) ? blockIdx.y * TY : 0;
@@ -164,7 +159,7 @@ template <int D, typename FS, int TX, int TY, int PF> struct TmaBlock {
             pphase ^= 1u << ps;
             p_pending &= ~(1u << ps);
         } else {
-            *abort_flag = 1;
+            timed_out = true;
         }
     }
     __device__ __forceinline__ void wait_b(int q) {
@@ -173,7 +168,7 @@ template <int D, typename FS, int TX, int TY, int PF> struct TmaBlock {
             bphase ^= 1u << bs;
             b_pending &= ~(1u << bs);
         } else {
-            *abort_flag = 1;
+            timed_out = true;
         }
     }
     __device__ __forceinline__ void drain() {
@@ -317,7 +312,7 @@ template <int D, typename FS, int TX, int TY, int PF> struct TmaBlock {
 
     // ---- stage 2: gradients, collision and store for tile site (tx, ty) at p ----
     __device__ __forceinline__ void stage2(int tx, int ty, int p, const real* c_df, const real* c_bt, real c_rho,
-                                           const real* c_j, real c_E, double* acc, int& bad) {
+                                           const real* c_j, real c_E, DiagAcc<real, D + 2>& acc, int& bad) {
         const long long s = (D == 3) ? (x0 + tx) + (long long)nx * ((y0 + ty) + (long long)ny * p)
                                      : (x0 + tx) + (long long)nx * p;
         const int rc = ((tx + 1) + RX * ((D == 3) ? ty + 1 : 0)) * NAP;
@@ -362,13 +357,11 @@ __global__ void __launch_bounds__(TmaShape<D, FS, TX, TY, PF>::NT, TmaShape<D, F
     constexpr int NINT = Sh::NINT, NRING = Sh::NRING, NT = Sh::NT, RX = Sh::RX;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int abort_flag;
-    TmaBlock<D, FS, TX, TY, PF> blk(ta, smem, &abort_flag);
+    TmaBlock<D, FS, TX, TY, PF> blk(ta, smem);
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int k = 0; k < Sh::NPS + Sh::NBS; ++k) mbar_init(blk.pbar() + k, 1);
         fence_barrier_init();
-        abort_flag = 0;
     }
     __syncthreads();
 
@@ -401,9 +394,7 @@ __global__ void __launch_bounds__(TmaShape<D, FS, TX, TY, PF>::NT, TmaShape<D, F
 
     real c_df[Q], c_bt[NB], c_rho = real(1), c_j[D], c_E = real(0);
     real n_df[Q], n_bt[NB], n_rho = real(1), n_j[D], n_E = real(0);
-    double acc[D + 2];
-#pragma unroll
-    for (int k = 0; k < D + 2; ++k) acc[k] = 0.0;
+    DiagAcc<real, D + 2> acc;
     int bad = 0;
 
     const int p0 = blk.p0, p1 = blk.p1;
@@ -448,9 +439,9 @@ __global__ void __launch_bounds__(TmaShape<D, FS, TX, TY, PF>::NT, TmaShape<D, F
         }
         // The one barrier per plane: the aux of plane q is complete, and all
         // reads of the population slot of q and the variance slot of q-1 are
-        // done, so thread 0 may refill them in the next iteration.
-        __syncthreads();
-        if (abort_flag) {
+        // done, so thread 0 may refill them in the next iteration.  It also
+        // tells every thread at once whether any wait gave up.
+        if (__syncthreads_or(blk.timed_out)) {
             aborted = true;
             break;
         }

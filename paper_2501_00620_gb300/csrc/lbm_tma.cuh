@@ -7,6 +7,10 @@
 
 namespace lbm {
 
+__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+constexpr uint64_t kWaitLimit = 20000000ull;  // ns before a wait for a tile copy gives up
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
