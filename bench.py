@@ -38,6 +38,9 @@ WORKLOAD_TEXT = {
     "sound1d": "D1Q3 256 periodic sound wave, rho=1+1e-3 sin(2 pi x/256), T0=1/3, tau=0.8; isothermal",
     "riemann1d": "D1Q3 4096 two-state Riemann (rho 1:0.125, T 1.0:0.8 x 0.15), tau=0.55; thermal; "
                  "fixed-state ends",
+    "serve": "serving mix: seeded Poisson arrivals at 200/s of 1000 requests, half D1Q3 (nx log-uniform "
+             "64-65536), half D2Q9 (N^2, N log-uniform 64-1024), half sound waves (tau 0.8, T0 1/3), half "
+             "Riemann (tau 0.55, T0 0.15, thermal, fixed-state x), steps uniform 100-5000; FP32",
 }
 
 
@@ -51,6 +54,12 @@ def parse():
     p.add_argument("--dtype", default=None, help="storage dtype override: f64 f32 f16 bf16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--scale", type=int, default=0,
+                   help="grid edge of a smaller instance of the workload (profiling captures); 0: full size")
+    p.add_argument("--tile", type=int, default=-1, help="force a kernel tile variant (-1: autotuned)")
+    p.add_argument("--chunk", type=int, default=0, help="force planes per block (0: autotuned)")
+    p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
+    p.add_argument("--no-sequential", action="store_true", help="serve: skip the one-at-a-time comparison")
     return p.parse_args()
 
 
@@ -146,18 +155,24 @@ def hbm_peak():
         return 6800.0, "of fallback"
 
 
+KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_tma.cuh",
+                  "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the device sources the step kernels are built from: an ncu
+    figure taken from other sources no longer describes the kernel."""
     h = hashlib.sha256()
-    for f in ("lbm_step.cuh", "lbm_lattice.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2501_00620_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, dtype):
+def profiled_traffic(kernel, workload, dtype):
     """DRAM bytes per launch from the committed ncu summary of this kernel and
     workload, if it was captured from the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "step_kernel_%s_%s.md" % (workload, dtype))
+    p = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kernel, workload, dtype))
     try:
         text = open(p).read()
     except OSError:
@@ -233,11 +248,49 @@ def run_oracle(name, n, steps, warmup):
     return sites * steps / dt / 1e6, dt, sites
 
 
+def reference_serve_sample(budget_s):
+    """The oracle over the serving mix in arrival order, each request run to
+    its full step count, until about budget_s of CPU time: MLUPS."""
+    import oracle
+    from paper_2501_00620_gb300 import workloads as W
+    t0 = time.perf_counter()
+    updates, n = 0.0, 0
+    for r in W.serving_requests(1000, 200.0, seed=0):
+        rho, u, T = W.request_fields(r)
+        tau, T0, thermal, bc = W.request_params(r)
+        s = oracle.Sim(r["dim"], r["nx"], r["ny"], 1, tau=tau, T0=T0, thermal=thermal, bc=bc)
+        s.init(rho, u, T)
+        s.step(r["steps"])
+        s.moments()
+        updates += r["nx"] * r["ny"] * r["steps"]
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return updates / dt / 1e6, dt, n
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     name = args.workload
+    if name == "serve":
+        import oracle
+        threads = oracle.set_threads(0)
+        mlups, dt, n = reference_serve_sample(20.0)
+        sample = "first %d requests of the serving mix, full step counts, %.1f s" % (n, dt)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": n, "warmup": 0, "ms_per_step": 1e3 * dt / max(n, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "reference": "FP64 CPU oracle (oracle/)",
+                       "step_unit": "one request"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     c = workload_params(name, None)
     n, threads, _ = oracle_sample(name, 120.0, args.steps + args.warmup)
     mlups, dt, sites = run_oracle(name, n, args.steps, args.warmup)
@@ -256,10 +309,132 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """The serving mix through the continuous-batching server, submitted in
+    real time; then, unless --no-sequential, the same requests one at a time
+    through the plain entry points (create, init, step, moments, destroy)."""
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_00620_gb300 import lbm
+    from paper_2501_00620_gb300 import workloads as W
+
+    reqs = W.serving_requests(args.requests, 200.0, seed=0)
+    sites = [r["nx"] * r["ny"] for r in reqs]
+    updates = float(sum(n * r["steps"] for n, r in zip(sites, reqs)))
+    bytes_alg = float(sum(n * r["steps"] * algorithmic_bytes_per_site(r["dim"], "f32")
+                          for n, r in zip(sites, reqs)))
+
+    def submit(srv, r):
+        rho, u, T = W.request_fields(r)
+        tau, T0, thermal, bc = W.request_params(r)
+        return srv.submit(r["dim"], r["nx"], r["ny"], tau, T0, thermal, bc, r["steps"], rho, u, T)
+
+    srv = lbm.Server()
+    for r in reqs[:8]:  # warm-up: kernel loading, first rounds
+        srv.wait(submit(srv, dict(r, steps=min(r["steps"], 50))))
+    base = srv.stats()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        delay = t0 + r["t_arrival"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(submit(srv, r))
+    results = [srv.wait(t, timeout=3600.0) for t in tickets]
+    lat = np.array([r[3] for r in results])
+    unstable = [dict(kind=q["kind"], dim=q["dim"], nx=q["nx"], steps=q["steps"])
+                for q, r in zip(reqs, results) if r.unstable]
+    st = srv.stats()
+    clocks = sampler.stop()
+    srv.close()
+    wall = st["last_done_s"] - max(st["first_submit_s"], base["last_done_s"])
+    tt = torch.tensor([wall], device="cuda")
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    wall = float(tt.item())
+    busy = st["busy_s"] - base["busy_s"]
+    rounds = st["rounds"] - base["rounds"]
+    value = world * updates / wall / 1e6
+
+    seq = None
+    if not args.no_sequential:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for r in reqs:
+            rho, u, T = W.request_fields(r)
+            tau, T0, thermal, bc = W.request_params(r)
+            sim = lbm.Simulation(r["dim"], r["nx"], r["ny"], 1, tau=tau, T0=T0, bc=bc, dtype="f32",
+                                 thermal=thermal, device=local)
+            sim.init(rho, u, T)
+            sim.step(r["steps"])
+            try:
+                sim.moments()
+            except lbm.LBMError as e:
+                if e.status != lbm.LBM_EUNSTABLE:
+                    raise
+            sim.close()
+        seq_s = time.perf_counter() - t1
+        seq = {"value": updates / seq_s / 1e6, "unit": "MLUPS", "wall_s": seq_s,
+               "how": "same requests in arrival order, one at a time: lbm_create, lbm_init, lbm_step, "
+                      "lbm_moments, lbm_destroy (FP32, autotuned single-simulation kernels)"}
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peak, peak_src = hbm_peak()
+    achieved = bytes_alg / busy / 1e9 if busy > 0 else None
+    h2d = float(sum((2 + r["dim"]) * n * 8 for n, r in zip(sites, reqs)))
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
+        "warmup": 8, "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "requests": len(reqs),
+                   "site_updates": updates, "step_unit": "one request (steps and ms_per_step count requests)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "kernel": "serve_kernel (cooperative, persistent over each round)"},
+        "serving": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "max_s": float(lat.max()), "wall_s": wall, "busy_s": busy, "rounds": rounds,
+                    "offered_mlups": updates / max(reqs[-1]["t_arrival"], 1e-9) / 1e6,
+                    "unstable_requests": len(unstable),
+                    "unstable_examples": unstable[:5],
+                    "sequential": seq},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": peak_src,
+                     "kernel": "serve_kernel", "launches": rounds,
+                     "duration": "CUDA events around each batched launch (busy_s)"},
+        "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / len(reqs),
+                "d2h_bytes_per_step": h2d / len(reqs),
+                "includes": "per request: fields copied in at submit, results copied out at completion; "
+                            "time from first submit to last completion"},
+        "gpu_launches": rounds,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     rank, world, local = dist_env()
     import numpy as np
@@ -276,13 +451,18 @@ def main():
 
     name = args.workload
     c = workload_params(name, args.dtype)
+    if args.scale:
+        c["nx"] = args.scale
+        c["ny"] = args.scale if c["d"] >= 2 else 1
+        c["nz"] = args.scale if c["d"] == 3 else 1
     d, nx, ny, nz = c["d"], c["nx"], c["ny"], c["nz"]
     N = nx * ny * nz
-    rho, u, T = W.fields_for(name)
+    rho, u, T = W.fields_for(name, scale=args.scale or None)
 
     stream = torch.cuda.Stream(device=local)
     sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=c["dtype"],
-                         thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True)
+                         thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True,
+                         tile=args.tile, chunk=args.chunk)
     sim.init(rho, u, T)
 
     def barrier():
@@ -320,7 +500,8 @@ def main():
     bps = algorithmic_bytes_per_site(d, c["dtype"])
     achieved = N * bps / (ms_per_step * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
-    traffic = profiled_traffic(name, c["dtype"])
+    tile, chunk, kernel = sim.launch_config()
+    traffic = profiled_traffic(kernel, name, c["dtype"])
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -373,10 +554,15 @@ def main():
         "config": {"workload": name + ": " + WORKLOAD_TEXT[name], "storage": c["dtype"],
                    "sites": N, "l2": "state of %.2f GB per buffer > 129 MB L2, no flush needed"
                    % (N * bps / 2 / 1e9) if N * bps / 2 > 2 * 129e6 else "flush not applied: small lattice",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "kernel": kernel, "tile": tile, "chunk": chunk,
+                   "edge": args.scale or None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": peak_src, "bytes_per_site": bps, "kernel": "step_kernel"},
+                     "peak_source": peak_src, "bytes_per_site": bps, "kernel": kernel,
+                     "launches": args.steps,
+                     "duration": "CUDA events on the launching stream around the timed steps, "
+                                 "one step-kernel launch per step"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps,

@@ -12,6 +12,7 @@ struct StepArgs {
     int chunk;            // planes per block along the march axis
     long long N;
     double omega, tau, T0;
+    float omega_f, tau_f, T0_f;  // the same, rounded to FP32 on the host (FP32 arithmetic)
     int thermal;
     int fixed_x;          // 1: frozen reservoirs outside [0, nx)
     long long rows;       // ny * nz (reservoir rows)
@@ -29,5 +30,27 @@ struct StepArgs {
     long long* step_ctr;  // device step counter (history index)
     int* flag;            // bit 0: fatal (rho <= 0 or non-finite); bit 1: T <= 0 seen
 };
+
+// omega, tau, T0 in the arithmetic type R (no per-site conversion from FP64).
+__host__ __device__ __forceinline__ void step_params(const StepArgs& a, double& omega, double& tau, double& T0) {
+    omega = a.omega;
+    tau = a.tau;
+    T0 = a.T0;
+}
+__host__ __device__ __forceinline__ void step_params(const StepArgs& a, float& omega, float& tau, float& T0) {
+    omega = a.omega_f;
+    tau = a.tau_f;
+    T0 = a.T0_f;
+}
+
+// Sets omega = 1/(tau + 1/2) (Eq. 55), tau, T0 and their FP32 copies.
+inline void set_step_params(StepArgs& a, double tau, double T0) {
+    a.omega = 1.0 / (tau + 0.5);
+    a.tau = tau;
+    a.T0 = T0;
+    a.omega_f = (float)a.omega;
+    a.tau_f = (float)tau;
+    a.T0_f = (float)T0;
+}
 
 }  // namespace lbm

@@ -129,9 +129,7 @@ StepArgs base_args(const lbm_sim* s) {
     a.nz = s->nz;
     a.chunk = s->chunk;
     a.N = s->N;
-    a.omega = 1.0 / (s->tau + 0.5);
-    a.tau = s->tau;
-    a.T0 = s->T0;
+    set_step_params(a, s->tau, s->T0);
     a.thermal = s->opts.thermal;
     a.fixed_x = s->bc == LBM_BC_FIXED_STATE;
     a.rows = s->rows;

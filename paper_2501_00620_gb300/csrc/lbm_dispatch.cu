@@ -23,39 +23,26 @@ LBM_DECLARE_D(2)
 LBM_DECLARE_D(3)
 #undef LBM_DECLARE_D
 
-#define LBM_DECLARE_TMA(DD)                                                          \
-    int n_tma_variants_d##DD();                                                      \
-    Variant tma_variant_d##DD(int v);                                                \
-    cudaError_t tma_box_d##DD(int dtype, int v, TmaBox* box);                         \
-    cudaError_t launch_step_tma_d##DD(int dtype, int v, const TmaArgs& ta, cudaStream_t st);
-LBM_DECLARE_TMA(2)
-LBM_DECLARE_TMA(3)
-#undef LBM_DECLARE_TMA
-
 #define LBM_BY_D(D, call1, call2, call3, bad) \
     ((D) == 1 ? (call1) : (D) == 2 ? (call2) : (D) == 3 ? (call3) : (bad))
 
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
 
-const char* kernel_name(int D, int v) {
-    if (v < kTmaBase) return "step_kernel";
-    const int nfast = D == 2 ? n_fast_variants_d2() : (D == 3 ? n_fast_variants_d3() : 0);
-    return v - kTmaBase >= n_tma_variants(D) - nfast ? "step_fast_kernel" : "step_tma_kernel";
-}
+const char* kernel_name(int D, int v) { return v < kTmaBase ? "step_kernel" : "step_fast_kernel"; }
 
-int n_tma_variants(int D) { return D == 2 ? n_tma_variants_d2() : (D == 3 ? n_tma_variants_d3() : 0); }
+int n_tma_variants(int D) { return D == 2 ? n_fast_variants_d2() : (D == 3 ? n_fast_variants_d3() : 0); }
 
 Variant variant(int D, int v) {
     if (v >= kTmaBase) {
         const int k = v - kTmaBase;
-        return D == 2 ? tma_variant_d2(k) : (D == 3 ? tma_variant_d3(k) : Variant{0, 0});
+        return D == 2 ? fast_variant_d2(k) : (D == 3 ? fast_variant_d3(k) : Variant{0, 0});
     }
     return LBM_BY_D(D, variant_d1(v), variant_d2(v), variant_d3(v), (Variant{0, 0}));
 }
 
 cudaError_t tma_box(int D, int dtype, int v, TmaBox* box) {
     const int k = v - kTmaBase;
-    return D == 2 ? tma_box_d2(dtype, k, box) : (D == 3 ? tma_box_d3(dtype, k, box) : cudaErrorInvalidValue);
+    return D == 2 ? fast_box_d2(dtype, k, box) : (D == 3 ? fast_box_d3(dtype, k, box) : cudaErrorInvalidValue);
 }
 
 size_t step_smem(int D, int dtype, int v) {
@@ -68,8 +55,8 @@ size_t step_smem(int D, int dtype, int v) {
 
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
     const int k = v - kTmaBase;
-    return D == 2 ? launch_step_tma_d2(dtype, k, ta, st)
-                  : (D == 3 ? launch_step_tma_d3(dtype, k, ta, st) : cudaErrorInvalidValue);
+    return D == 2 ? launch_step_fast_d2(dtype, k, ta, st)
+                  : (D == 3 ? launch_step_fast_d3(dtype, k, ta, st) : cudaErrorInvalidValue);
 }
 
 dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk) {

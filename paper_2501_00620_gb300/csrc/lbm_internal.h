@@ -16,7 +16,7 @@ struct Variant {
 };
 
 // Variant indices: 0..n_variants(D)-1 select the generic kernel's tiles;
-// kTmaBase + k selects the k-th tile of the TMA-staged kernel.
+// kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;
 
 // Slice geometry of a TMA variant (for the host-side tensor maps).

@@ -253,7 +253,8 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
     using L = Lattice<D>;
     using breal = typename Store<FS>::breal;
     const long long N = a.N;
-    const R omega = R(a.omega), tau = R(a.tau), T0 = R(a.T0);
+    R omega, tau, T0;
+    step_params(a, omega, tau, T0);
     R trG = R(-0.0);
 #pragma unroll
     for (int c = 0; c < D; ++c) trG += G[c];

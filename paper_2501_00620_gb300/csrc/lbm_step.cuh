@@ -73,7 +73,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
     const int p0 = (D == 1) ? 0 : bz * a.chunk;
     const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np);
     const long long N = a.N;
-    const real omega = real(a.omega), T0 = real(a.T0);
+    real omega, tau, T0;
+    step_params(a, omega, tau, T0);
+    (void)tau;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     // interior site of this thread in region coordinates

@@ -262,7 +262,9 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             for (int k = 0; k < NB; ++k) bsum[k] += fi * bsrc[k * Sh::BSLICE + offb];
         }
         real u0[D], rb[NB], bt[NB], rho, j[D], E;
-        site_moments<D, real>(df, bsum, real(a.omega), real(a.T0), a.thermal, bt, rho, j, E, u0, rb);
+        real omega, tau, T0;
+        step_params(a, omega, tau, T0);
+        site_moments<D, real>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
         if (tile) {
             real* v = sv(q);
             constexpr int NI = Sh::NINT;

@@ -63,6 +63,41 @@ class LBMError(RuntimeError):
         self.status = status
 
 
+class lbm_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t),
+                ("max_active", ctypes.c_int),
+                ("device", ctypes.c_int),
+                ("round_ms", ctypes.c_double)]
+
+
+class lbm_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int),
+                ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int),
+                ("tau", ctypes.c_double),
+                ("T0", ctypes.c_double),
+                ("thermal", ctypes.c_int),
+                ("bc", ctypes.c_int),
+                ("steps", ctypes.c_long),
+                ("rho", ctypes.POINTER(ctypes.c_double)),
+                ("u", ctypes.POINTER(ctypes.c_double)),
+                ("T", ctypes.POINTER(ctypes.c_double))]
+
+
+class lbm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64),
+                ("active", ctypes.c_int),
+                ("queued", ctypes.c_int),
+                ("site_updates", ctypes.c_double),
+                ("busy_s", ctypes.c_double),
+                ("rounds", ctypes.c_uint64),
+                ("first_submit_s", ctypes.c_double),
+                ("last_done_s", ctypes.c_double),
+                ("pool_bytes", ctypes.c_size_t),
+                ("pool_in_use", ctypes.c_size_t)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("liblbm.so is not built (run __graft_entry__.build() or "
@@ -89,16 +124,28 @@ def _load():
     L.lbm_flags.restype = ctypes.c_int
     L.lbm_step_count.argtypes = [vp]
     L.lbm_step_count.restype = ctypes.c_long
+    L.lbm_launch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_char_p)]
     L.lbm_save.argtypes = [vp, ctypes.c_char_p]
     L.lbm_load.argtypes = [vp, ctypes.c_char_p]
     L.lbm_step_noalloc.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_double, ctypes.c_int] + [vp] * 6
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_server_default_opts.argtypes = [ctypes.POINTER(lbm_server_opts)]
+    L.lbm_server_default_opts.restype = None
+    L.lbm_server_create.argtypes = [ctypes.POINTER(lbm_server_opts), ctypes.POINTER(vp)]
+    L.lbm_server_submit.argtypes = [vp, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.lbm_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(lbm_fields_out), dp]
+    L.lbm_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(lbm_fields_out), dp]
+    L.lbm_server_stats_get.argtypes = [vp, ctypes.POINTER(lbm_server_stats)]
+    L.lbm_server_destroy.argtypes = [vp]
+    L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
-                 "lbm_save", "lbm_load", "lbm_step_noalloc"):
+                 "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
+                 "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -188,6 +235,13 @@ def lbm_flags(sim):
 
 def lbm_step_count(sim):
     return _lib.lbm_step_count(sim)
+
+
+def lbm_launch_config(sim):
+    """(tile, chunk, kernel name) of the step launches; (-1, -1, '') before the first step."""
+    t, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_char_p()
+    _check(_lib.lbm_launch_config(sim, ctypes.byref(t), ctypes.byref(c), ctypes.byref(k)))
+    return t.value, c.value, (k.value or b"").decode()
 
 
 def lbm_save(sim, path):
@@ -330,8 +384,99 @@ class Simulation:
         b = np.ascontiguousarray(b, dtype=np.float64)
         lbm_set_state(self.h, f, b)
 
+    def launch_config(self):
+        return lbm_launch_config(self.h)
+
     def save(self, path):
         lbm_save(self.h, path)
 
     def load(self, path):
         lbm_load(self.h, path)
+
+
+# ---------------------------------------------------------------------------
+# Serving (include/lbm_serve.h)
+
+def lbm_server_default_opts():
+    o = lbm_server_opts()
+    _lib.lbm_server_default_opts(ctypes.byref(o))
+    return o
+
+
+class ServeResult(tuple):
+    """(rho, u, T, latency_s) of a finished request; ``unstable`` is True when
+    the simulation became non-physical (the fields are those it reached)."""
+    unstable = False
+
+
+class Server:
+    """Continuous-batching service for D1Q3 / D2Q9 requests (FP32)."""
+
+    def __init__(self, hbm_budget=0, max_active=0, device=0, round_ms=0.0):
+        o = lbm_server_default_opts()
+        o.hbm_budget = int(hbm_budget)
+        if max_active:
+            o.max_active = int(max_active)
+        o.device = device
+        if round_ms:
+            o.round_ms = float(round_ms)
+        h = ctypes.c_void_p()
+        _check(_lib.lbm_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self._shapes = {}
+
+    def submit(self, dim, nx, ny, tau, T0, thermal, bc, steps, rho, u, T):
+        """Queue one request; rho, T of N values and u of dim x N (any shape). Returns the ticket."""
+        N = nx * ny
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(N)
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(N)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(dim * N)
+        q = lbm_request(dim, nx, ny, float(tau), float(T0), int(bool(thermal)),
+                        BCS[bc] if isinstance(bc, str) else int(bc), int(steps), _dp(rho), _dp(u), _dp(T))
+        t = ctypes.c_uint64()
+        _check(_lib.lbm_server_submit(self.h, ctypes.byref(q), ctypes.byref(t)))
+        self._shapes[t.value] = (dim, ny, nx)
+        return t.value
+
+    def _result(self, fn, ticket, *extra):
+        dim, ny, nx = self._shapes[ticket]
+        rho = np.empty((ny, nx))
+        u = np.empty((dim, ny, nx))
+        T = np.empty((ny, nx))
+        lat = ctypes.c_double()
+        out = lbm_fields_out(_dp(rho), _dp(u), _dp(T))
+        st = fn(self.h, ctypes.c_uint64(ticket), *extra, ctypes.byref(out), ctypes.byref(lat))
+        if st == LBM_EBUSY:
+            return None
+        if st not in (LBM_OK, LBM_EUNSTABLE):
+            _check(st)
+        del self._shapes[ticket]
+        r = ServeResult((rho, u, T, lat.value))
+        r.unstable = st == LBM_EUNSTABLE
+        return r
+
+    def poll(self, ticket):
+        """ServeResult (rho, u, T, latency_s) once done, else None."""
+        return self._result(_lib.lbm_server_poll, ticket)
+
+    def wait(self, ticket, timeout=600.0):
+        r = self._result(_lib.lbm_server_wait, ticket, ctypes.c_double(timeout))
+        if r is None:
+            raise LBMError(LBM_EBUSY, "request %d not finished after %.0f s" % (ticket, timeout))
+        return r
+
+    def stats(self):
+        st = lbm_server_stats()
+        _check(_lib.lbm_server_stats_get(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in lbm_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
