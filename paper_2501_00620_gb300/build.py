@@ -29,8 +29,15 @@ def nvcc():
     return p
 
 
+# Translation units that take longest to compile start first.
+_HEAVY = ("gen3", "fast3", "fast2", "serve", "noalloc", "d2")
+
+
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    def rank(p):
+        b = os.path.basename(p)
+        return next((k for k, h in enumerate(_HEAVY) if h in b), len(_HEAVY)), b
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")), key=rank)
 
 
 def _headers():

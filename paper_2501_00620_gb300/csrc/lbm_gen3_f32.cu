@@ -1,0 +1,6 @@
+// Generic D3 step kernel, float storage (see lbm_gen3.cuh).
+#include "lbm_gen3.cuh"
+
+namespace lbm {
+LBM_GEN3_DEFINE(float)
+}  // namespace lbm

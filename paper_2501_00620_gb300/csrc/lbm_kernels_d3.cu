@@ -1,51 +1,13 @@
-// Launchers for the D3 lattice (tile variants x storage types).
-#include "lbm_internal.h"
+// Launchers for the D3 lattice: storage-type dispatch, init, reservoir and
+// state kernels.  The generic step kernel is instantiated per storage type in
+// lbm_gen3_*.cu (one translation unit each, so that they compile in parallel).
+#include "lbm_gen3.cuh"
 
 namespace lbm {
 
 namespace {
 constexpr int kD = 3;
-constexpr Variant kVariants[] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}};
-constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
-
-template <typename FS, int TX, int TY>
-cudaError_t launch_one(const StepArgs& a, cudaStream_t st) {
-    using Sh = StepShape<kD, FS, TX, TY>;
-    auto kern = step_kernel<kD, FS, TX, TY>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid = step_grid(kD, -1, a.nx, a.ny, a.nz, a.chunk);
-    grid.x = (a.nx + TX - 1) / TX;
-    if (kD == 3) grid.y = (a.ny + TY - 1) / TY;
-    kern<<<grid, TX * TY, Sh::smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename FS>
-cudaError_t launch_dtype(int v, const StepArgs& a, cudaStream_t st) {
-    switch (v) {
-        case 0: return launch_one<FS, 32, 8>(a, st);
-        case 1: return launch_one<FS, 32, 4>(a, st);
-        case 2: return launch_one<FS, 64, 4>(a, st);
-        case 3: return launch_one<FS, 32, 16>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename FS>
-size_t smem_of(int v) {
-    switch (v) {
-        case 0: return StepShape<kD, FS, 32, 8>::smem;
-        case 1: return StepShape<kD, FS, 32, 4>::smem;
-        case 2: return StepShape<kD, FS, 64, 4>::smem;
-        case 3: return StepShape<kD, FS, 32, 16>::smem;
-        default: return 0;
-    }
-}
+constexpr int kNV = kGen3Tiles;
 
 template <typename F>
 cudaError_t by_dtype(int dtype, F&& f) {
@@ -62,21 +24,21 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 }  // namespace
 
 cudaError_t launch_step_d3(int dtype, int v, const StepArgs& a, cudaStream_t st) {
-    return by_dtype(dtype, [&](auto tag) { return launch_dtype<decltype(tag)>(v, a, st); });
+    return by_dtype(dtype, [&](auto tag) { return gen3_launch<decltype(tag)>(v, a, st); });
 }
 
 size_t step_smem_d3(int dtype, int v) {
     switch (dtype) {
-        case DT_F64: return smem_of<double>(v);
-        case DT_F32: return smem_of<float>(v);
-        case DT_F16: return smem_of<__half>(v);
-        case DT_BF16: return smem_of<__nv_bfloat16>(v);
+        case DT_F64: return gen3_smem<double>(v);
+        case DT_F32: return gen3_smem<float>(v);
+        case DT_F16: return gen3_smem<__half>(v);
+        case DT_BF16: return gen3_smem<__nv_bfloat16>(v);
     }
     return 0;
 }
 
 int n_variants_d3() { return kNV; }
-Variant variant_d3(int v) { return kVariants[v]; }
+Variant variant_d3(int v) { return gen3_tile(v); }
 
 cudaError_t launch_init_d3(int dtype, const double* rho, const double* u, const double* T, void* f, void* b,
                             long long N, cudaStream_t st) {
