@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <cstdio>
@@ -195,20 +196,21 @@ lbm_status tma_maps(lbm_sim* s, int v, int buf, TmaArgs* ta) {
             if (s->D == 3) {
                 cuuint64_t gd[4] = {nx, ny, nz, (cuuint64_t)s->Q};
                 cuuint64_t gs[3] = {nx * es, nx * ny * es, N * es};
-                cuuint32_t bx[4] = {(cuuint32_t)box.sxf, (cuuint32_t)box.sy, 1, 1};
+                cuuint32_t bx[4] = {(cuuint32_t)box.sxf, (cuuint32_t)box.sy, 1, (cuuint32_t)s->Q};
                 r1 = enc(&maps[k].first, dt, 4, s->f[k], gd, gs, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                cuuint64_t gdb[4] = {nx, ny, nz, (cuuint64_t)s->NB};
-                cuuint64_t gsb[3] = {nx * 4, nx * ny * 4, N * 4};
-                cuuint32_t bxb[4] = {(cuuint32_t)box.sxb, (cuuint32_t)box.sy, 1, (cuuint32_t)s->NB};
+                // variance: three planes of component pairs, (2 nx) floats per row
+                cuuint64_t gdb[4] = {2 * nx, ny, nz, (cuuint64_t)s->NB / 2};
+                cuuint64_t gsb[3] = {2 * nx * 4, 2 * nx * ny * 4, 2 * N * 4};
+                cuuint32_t bxb[4] = {2 * (cuuint32_t)box.sxb, (cuuint32_t)box.sy, 1, (cuuint32_t)s->NB / 2};
                 r2 = enc(&maps[k].second, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->b[k], gdb, gsb, bxb, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             } else {
                 cuuint64_t gd[3] = {nx, ny, (cuuint64_t)s->Q};
                 cuuint64_t gs[2] = {nx * es, N * es};
-                cuuint32_t bx[3] = {(cuuint32_t)box.sxf, 1, 1};
+                cuuint32_t bx[3] = {(cuuint32_t)box.sxf, 1, (cuuint32_t)s->Q};
                 r1 = enc(&maps[k].first, dt, 3, s->f[k], gd, gs, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -266,7 +268,8 @@ std::vector<int> chunk_candidates(const lbm_sim* s) {
 }
 
 lbm_status ensure_partial(lbm_sim* s, int v, int chunk) {
-    size_t nb = blocks_of(s, v, chunk);
+    // at least 8 blocks per multiprocessor: the persistent step grids
+    size_t nb = std::max(blocks_of(s, v, chunk), (size_t)8 * device_sms());
     if (nb <= s->partial_blocks) return LBM_OK;
     double* p = (double*)s->dalloc(nb * (s->D + 2) * sizeof(double));
     if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");

@@ -26,6 +26,18 @@ LBM_DECLARE_D(3)
 #define LBM_BY_D(D, call1, call2, call3, bad) \
     ((D) == 1 ? (call1) : (D) == 2 ? (call2) : (D) == 3 ? (call3) : (bad))
 
+int device_sms() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
 
 const char* kernel_name(int D, int v) { return v < kTmaBase ? "step_kernel" : "step_fast_kernel"; }

@@ -2,26 +2,31 @@
 // the tile table per lattice and one launcher per (storage, tile, boundary).
 #pragma once
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 #include "lbm_step_fast.cuh"
 
 namespace lbm {
 
-// Tile TX x TY, extra variance prefetch planes PFB, resident blocks per SM MB.
+// Tile TX x TY, extra variance prefetch planes PFB, resident blocks per SM MB,
+// persistent grid (balanced shares of the column x plane work) or one block
+// per (tile, chunk).
 struct FastVariant {
-    int tx, ty, pfb, mb;
+    int tx, ty, pfb, mb, persist;
 };
 
-// D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 16 at one (less
-// ring recomputation); 32 x 4 with one more variance plane in flight.
-constexpr FastVariant kFast3[] = {{32, 8, 0, 2}, {32, 4, 0, 3}, {32, 16, 0, 1}, {32, 4, 1, 3}};
-// D2Q9: strips of 128 or 64 sites.
-constexpr FastVariant kFast2[] = {{128, 1, 0, 5}, {128, 1, 1, 5}, {64, 1, 0, 8}, {128, 1, 0, 6}};
+// D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 8 persistent;
+// 32 x 4 with one more variance plane in flight.
+constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 8, 0, 2, 1}, {32, 4, 1, 3, 0}};
+// D2Q9: strips of 128 or 64 sites; 128 persistent.
+constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {64, 1, 0, 8, 0}, {128, 1, 0, 5, 1}};
 
-template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX>
+
+template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX, bool PERSIST>
 cudaError_t launch_fast(const TmaArgs& ta, cudaStream_t st) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
-    auto kern = step_fast_kernel<D, FS, TX, TY, PFB, MB, FX>;
+    auto kern = step_fast_kernel<D, FS, TX, TY, PFB, MB, FX, PERSIST>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
@@ -31,6 +36,10 @@ cudaError_t launch_fast(const TmaArgs& ta, cudaStream_t st) {
     const StepArgs& a = ta.s;
     const int np = D == 3 ? a.nz : a.ny;
     dim3 grid(a.nx / TX, D == 3 ? a.ny / TY : 1, (np + a.chunk - 1) / a.chunk);
+    if (PERSIST) {
+        const long long work = (long long)grid.x * grid.y * np;
+        grid = dim3((unsigned)std::min<long long>(work, (long long)device_sms() * MB), 1, 1);
+    }
     kern<<<grid, Sh::NT, Sh::SMEM, st>>>(ta);
     return cudaGetLastError();
 }
@@ -39,7 +48,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB>
 void fast_box(TmaBox* b) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
     b->pxf = 16 / (int)sizeof(FS);
-    b->sxf = TX + 2 * b->pxf;  // population map (unused by this kernel, kept valid)
+    b->sxf = TX + 2 * b->pxf;  // population map: L2 prefetch box
     b->sxb = Sh::SXB;
     b->sy = Sh::SY;
     b->smem = Sh::SMEM;
@@ -53,7 +62,7 @@ void fast_box(TmaBox* b) {
             fast_box<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb>(box);                          \
             return cudaSuccess;                                                                         \
         }                                                                                               \
-        return launch_fast<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb, FX>(*ta, st);
+        return launch_fast<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb, FX, (TAB[K].persist != 0)>(*ta, st);
 
 template <int D, typename FS, bool FX>
 cudaError_t fast_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t st) {

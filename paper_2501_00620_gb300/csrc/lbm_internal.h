@@ -24,6 +24,9 @@ struct TmaBox {
     int sxf, sxb, sy, pxf, smem;
 };
 
+// Multiprocessor count of the current device (cached per device).
+int device_sms();
+
 int n_variants(int D);
 // Name of the kernel template variant v launches (for reports).
 const char* kernel_name(int D, int v);

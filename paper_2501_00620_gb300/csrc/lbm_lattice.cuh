@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -172,34 +174,47 @@ template <typename S> struct Store;
 template <> struct Store<double> {
     using real = double;
     using breal = double;
-    __device__ __forceinline__ static double ld(const double* p, long long k) { return __ldg(p + k); }
-    __device__ __forceinline__ static void st(double* p, long long k, double v) { p[k] = v; }
+    template <typename I> __device__ __forceinline__ static double ld(const double* p, I k) { return __ldg(p + k); }
+    template <typename I> __device__ __forceinline__ static void st(double* p, I k, double v) { p[k] = v; }
 };
 
 template <> struct Store<float> {
     using real = float;
     using breal = float;
-    __device__ __forceinline__ static float ld(const float* p, long long k) { return __ldg(p + k); }
-    __device__ __forceinline__ static void st(float* p, long long k, float v) { p[k] = v; }
+    template <typename I> __device__ __forceinline__ static float ld(const float* p, I k) { return __ldg(p + k); }
+    template <typename I> __device__ __forceinline__ static void st(float* p, I k, float v) { p[k] = v; }
 };
 
 template <> struct Store<__half> {
     using real = float;
     using breal = float;
-    __device__ __forceinline__ static float ld(const __half* p, long long k) {
+    template <typename I> __device__ __forceinline__ static float ld(const __half* p, I k) {
         return __half2float(__ldg(p + k));
     }
-    __device__ __forceinline__ static void st(__half* p, long long k, float v) { p[k] = __float2half_rn(v); }
+    template <typename I> __device__ __forceinline__ static void st(__half* p, I k, float v) { p[k] = __float2half_rn(v); }
 };
 
 template <> struct Store<__nv_bfloat16> {
     using real = float;
     using breal = float;
-    __device__ __forceinline__ static float ld(const __nv_bfloat16* p, long long k) {
+    template <typename I> __device__ __forceinline__ static float ld(const __nv_bfloat16* p, I k) {
         return __bfloat162float(__ldg(p + k));
     }
-    __device__ __forceinline__ static void st(__nv_bfloat16* p, long long k, float v) {
+    template <typename I> __device__ __forceinline__ static void st(__nv_bfloat16* p, I k, float v) {
         p[k] = __float2bfloat16_rn(v);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Layout of the variance planes of a state buffer (N sites).  FP64 storage and
+// the D1/D2 lattices: component-major, component k of site s at k N + s.
+// D3 with 32/16-bit storage: three planes of component pairs (xx, yy),
+// (zz, xy), (xz, yz) interleaved per site, component k at (k/2) 2N + 2s + k%2,
+// so that the transport reads a pair with one 8-byte access.
+template <int D, typename FS> struct BLayout {
+    static constexpr bool paired = D == 3 && !std::is_same<FS, double>::value;
+    __host__ __device__ static constexpr long long at(int k, long long s, long long N) {
+        return paired ? (long long)(k >> 1) * 2 * N + 2 * s + (k & 1) : (long long)k * N + s;
     }
 };
 

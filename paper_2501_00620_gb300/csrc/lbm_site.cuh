@@ -171,8 +171,8 @@ __device__ __forceinline__ void fd_add(int i, const R* rbn, const R* un, R* F, R
 // second-order Hermite projection whose zeroth, first and second moments are
 // 0, F and G (Eqs. 58-61) -- adds w_i tau (9/2 e_i.G.e_i - 3/2 tr G) to the
 // even part and 3 w_i tau e_i.F to the odd part.
-template <int D, typename FS, typename R>
-__device__ __forceinline__ void collide_store(FS* __restrict__ fo, long long N, const R* df, R rho, const R* u,
+template <int D, typename FS, typename R, typename I = long long>
+__device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R* df, R rho, const R* u,
                                               const R* F, const R* G, R trG, R omega, R tau) {
     using L = Lattice<D>;
     constexpr int Q = L::Q, NB = L::NB;
@@ -246,13 +246,14 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, long long N, 
 // fbar* = fbar + omega (f^eq + tau Phi - fbar) (Eq. 55, Appendix A, Eqs. 58-61)
 // and bbar* = bbar + omega (b^eq - bbar) (Eqs. 63, 65), stored at site s.
 // bad |= 1: rho <= 0 or non-finite; bad |= 2: T <= 0 in thermal mode.
-template <int D, typename FS, typename R>
-__device__ __forceinline__ void site_collide(const StepArgs& a, long long s, const R* c_df, const R* c_bt, R rho,
-                                             const R* c_j, R c_E, const R* F, const R* G, DiagAcc<R, D + 2>& acc,
-                                             int& bad) {
+// I is the index type of the site (int where the lattice has fewer than 2^31
+// sites); Acc the diagnostics accumulator (DiagAcc or a kernel's own).
+template <int D, typename FS, typename R, typename I = long long, typename Acc = DiagAcc<R, D + 2>>
+__device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_df, const R* c_bt, R rho,
+                                             const R* c_j, R c_E, const R* F, const R* G, Acc& acc, int& bad) {
     using L = Lattice<D>;
     using breal = typename Store<FS>::breal;
-    const long long N = a.N;
+    const I N = (I)a.N;
     R omega, tau, T0;
     step_params(a, omega, tau, T0);
     R trG = R(-0.0);
@@ -289,8 +290,8 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
         a.mout[(1 + D) * N + s] = double(Tm);
     }
     if (!a.write_state) return;
-    collide_store<D, FS, R>(static_cast<FS*>(a.fout) + s, N, c_df, rho, u, F, G, trG, omega, tau);
-    breal* __restrict__ bo = static_cast<breal*>(a.bout) + s;
+    collide_store<D, FS, R, I>(static_cast<FS*>(a.fout) + s, N, c_df, rho, u, F, G, trG, omega, tau);
+    breal* __restrict__ bo = static_cast<breal*>(a.bout);
     R bnew[L::NB];
 #pragma unroll
     for (int c = 0; c < D; ++c)
@@ -300,10 +301,13 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
             const R beq = u[c] * u[d2] * R(1.0 / 3.0) + (c == d2 ? T : R(0));
             bnew[k] = c_bt[k] + omega * (beq - c_bt[k]);
         }
+    if constexpr (BLayout<D, FS>::paired) {
+        float2* __restrict__ bo2 = reinterpret_cast<float2*>(bo);
 #pragma unroll
-    for (int k = 0; k < L::NB; ++k) {
-        bo[0] = breal(bnew[k]);
-        bo += N;
+        for (int p = 0; p < L::NB / 2; ++p) bo2[p * N + s] = make_float2(float(bnew[2 * p]), float(bnew[2 * p + 1]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::NB; ++k) bo[k * N + s] = breal(bnew[k]);
     }
 }
 
@@ -311,8 +315,8 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, long long s, con
 // then warps in order), per-block partials, and the last block's fixed-order
 // sum of all partials into the history record / diag_out.  `red` holds
 // 32 * (D + 2) doubles of shared memory.
-template <int D, int NT, typename R>
-__device__ __forceinline__ void block_diagnostics(const StepArgs& a, const DiagAcc<R, D + 2>& acc, double* red) {
+template <int D, int NT, typename Acc>
+__device__ __forceinline__ void block_diagnostics(const StepArgs& a, const Acc& acc, double* red) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll

@@ -148,7 +148,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
                 const long long s = sx + (long long)nx * (sy + (long long)ny * sz);
                 v = Store<FS>::ld(fin, (long long)i * N + s);
 #pragma unroll
-                for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + (long long)k * N + s));
+                for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + BLayout<D, FS>::at(k, s, N)));
             }
             df[i] = v;
             const real fi = real(L::w(i)) + v;
@@ -275,7 +275,7 @@ __global__ void init_kernel(const double* __restrict__ rho, const double* __rest
     for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int d2 = c; d2 < D; ++d2)
-            b[sym<D>(c, d2) * N + s] = uu[c] * uu[d2] * real(1.0 / 3.0) + (c == d2 ? real(T[s]) : real(0));
+            b[BLayout<D, FS>::at(sym<D>(c, d2), s, N)] = uu[c] * uu[d2] * real(1.0 / 3.0) + (c == d2 ? real(T[s]) : real(0));
 }
 
 // Reservoirs of the fixed-state boundary: for each row, the equilibrium of the
@@ -325,7 +325,7 @@ __global__ void get_state_kernel(const FS* __restrict__ f, const typename Store<
         for (int i = 0; i < L::Q; ++i) fo[i * N + s] = L::w(i) + double(Store<FS>::ld(f, i * N + s));
     if (bo)
 #pragma unroll
-        for (int k = 0; k < L::NB; ++k) bo[k * N + s] = double(b[k * N + s]) - (k < D ? 1.0 / 3.0 : 0.0);
+        for (int k = 0; k < L::NB; ++k) bo[k * N + s] = double(b[BLayout<D, FS>::at(k, s, N)]) - (k < D ? 1.0 / 3.0 : 0.0);
 }
 
 template <int D, typename FS>
@@ -341,7 +341,7 @@ __global__ void set_state_kernel(FS* __restrict__ f, typename Store<FS>::breal* 
         for (int i = 0; i < L::Q; ++i) Store<FS>::st(f, i * N + s, real(fi[i * N + s] - L::w(i)));
     if (bi)
 #pragma unroll
-        for (int k = 0; k < L::NB; ++k) b[k * N + s] = breal(bi[k * N + s] + (k < D ? 1.0 / 3.0 : 0.0));
+        for (int k = 0; k < L::NB; ++k) b[BLayout<D, FS>::at(k, s, N)] = breal(bi[k * N + s] + (k < D ? 1.0 / 3.0 : 0.0));
 }
 
 }  // namespace lbm

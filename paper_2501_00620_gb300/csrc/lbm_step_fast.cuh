@@ -1,23 +1,29 @@
 // Fused step of the bump-function lattice Boltzmann method (arXiv 2501.00620,
-// Sec. II.C) for D2Q9 / D3Q19 with FP32 or 16-bit population storage, laid
-// out for occupancy on sm_103a.  The per-site arithmetic is the one of the
-// other step kernels (lbm_site.cuh); only the data movement differs.
+// Sec. II.C) for D2Q9 / D3Q19 with FP32 or 16-bit population storage, written
+// for instruction economy on sm_103a.  The arithmetic is the one of the
+// generic kernel (lbm_step.cuh, lbm_site.cuh) up to FP32 rounding order; only
+// the data movement and the instruction selection differ.
 //
-// * Populations are pulled straight from global memory (read-only path).
-//   The pull is a permutation -- every emitted value is read by exactly one
-//   site -- so staging them in shared memory buys no reuse; leaving them out
-//   frees shared memory for more resident blocks.
+// * Populations are pulled straight from global memory (read-only path) with
+//   32-bit offsets from per-plane base pointers.  The pull is a permutation --
+//   every emitted value is read by exactly one site -- so staging them in
+//   shared memory would buy no reuse.
 // * The variance planes, which the mass-weighted transport (Eq. 66) reads at
 //   all Q neighbours, are staged by tiled bulk tensor copies (TMA) in a ring
-//   of 3 + PFB plane slots.  The copy of plane q+2+PFB is issued right after
-//   the block barrier that frees its slot, so it lands while stage 2 runs.
+//   of 3 + PFB plane slots.  In 3D they are stored as component pairs, so the
+//   transport reads one 8-byte pair per neighbour and accumulates it with the
+//   packed FP32x2 multiply-add of sm_100+ (two FP32 FMAs per instruction).
 // * (u0, rho b) of the tile plus a one-site ring live in four shared plane
-//   slots (stage 1 writes plane q; stage 2 of plane q-1 reads q-2 .. q), so
-//   one block barrier per plane suffices.
+//   slots, site-major as float2 pairs grouped by the rows of rho b that a
+//   neighbour direction needs; the gradient (Eqs. 59, 61) loads only those
+//   pairs, folds the sign of e_i into the adds, and applies the lattice
+//   weights once at the end (axis terms first, scaled by w_axis / w_edge).
 // * A tile site hands (bbar, rho, j0, Ebar) from stage 1 to stage 2 through
 //   its own column of two shared slots (plane parity) and pulls its
-//   populations a second time in stage 2 (cache hits); nothing is carried in
-//   registers across the barrier, which keeps MB blocks per SM resident.
+//   populations a second time in stage 2.
+// * The conservation diagnostics are summed per thread in FP32 as deviations
+//   from the rest state (rho - 1, E - D T0), which keeps the per-thread sums
+//   small and exact to far below the storage rounding; blocks reduce in FP64.
 //
 // A block owns a TX x TY tile (2D: a TX-wide strip) and marches along the
 // slowest axis (z in 3D, y in 2D) over `chunk` planes.  Threads: one per tile
@@ -26,35 +32,63 @@
 // (frozen equilibrium reservoirs); otherwise every axis is periodic.
 #pragma once
 
+#include <utility>
+
 #include "lbm_site.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
 
+// FP32 accumulator of the conservation diagnostics (mass, momentum, energy)
+// as deviations from the rest state: mass as rho - 1, energy as E - eref with
+// eref = D T0.  get() adds the references back in FP64.
+template <int K> struct DiagDev {
+    float d[K];
+    int n;
+    float eref;
+    __device__ __forceinline__ explicit DiagDev(float e) : n(0), eref(e) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = 0.0f;
+    }
+    __device__ __forceinline__ void add(int k, float x) {
+        if (k == 0) {
+            d[0] += x - 1.0f;
+            ++n;
+        } else if (k == K - 1) {
+            d[k] += x - eref;
+        } else {
+            d[k] += x;
+        }
+    }
+    __device__ __forceinline__ double get(int k) const {
+        return double(d[k]) + (k == 0 ? double(n) : (k == K - 1 ? double(n) * double(eref) : 0.0));
+    }
+};
+
 template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape {
     using L = Lattice<D>;
-    static constexpr int Q = L::Q, NB = L::NB, NAUX = D + NB;
+    static constexpr int Q = L::Q, NB = L::NB;
     static constexpr int PXB = 4;                                   // 16-byte aligned x start of a b copy
-    static constexpr int SXB = TX + 2 * PXB;
+    static constexpr int SXB = TX + 2 * PXB;                        // sites per staged row
     static constexpr int SY = (D == 3) ? TY + 4 : 1;
     static constexpr int RX = TX + 2;
     static constexpr int RY = (D == 3) ? TY + 2 : 1;
     static constexpr int RS = RX * RY;
-    static constexpr int NAP = round_up(NAUX, 2);                   // aux floats per site (site-major)
+    static constexpr int NA2 = (D == 3) ? 5 : 3;                    // float2 of (u0, rho b) per site
     static constexpr int NINT = TX * ((D == 3) ? TY : 1);
     static constexpr int NRING = RS - NINT;
     static constexpr int NT = round_up(NINT + NRING, 32);
-    static constexpr int BSLICE = SY * SXB;                         // floats of one variance component
+    static constexpr int BSLICE = SY * SXB;                         // sites of one staged slice
     static constexpr int BPITCH = round_up(NB * BSLICE * 4, 128);   // bytes between variance slots
     static constexpr int NBS = 3 + PFB, NAS = 4;
     static constexpr int NSV = NB + D + 2;                          // carried site values: bbar, rho, j0, Ebar
     static constexpr int OFF_AUX = NBS * BPITCH;
-    static constexpr int OFF_SV = OFF_AUX + round_up(NAS * NAP * RS * 4, 16);
+    static constexpr int OFF_SV = OFF_AUX + round_up(NAS * NA2 * 8 * RS, 16);
     static constexpr int OFF_RED = OFF_SV + 2 * NSV * NINT * 4;
     static constexpr int OFF_BAR = OFF_RED + 32 * (D + 2) * 8;
     static constexpr int SMEM = OFF_BAR + NBS * 8;
     static constexpr uint32_t BBYTES = NB * BSLICE * 4;             // transaction bytes per variance slot
-    static_assert(SXB <= 256 && SY <= 256, "TMA box edges are limited to 256 elements");
+    static_assert((D == 3 ? 2 * SXB : SXB) <= 256 && SY <= 256, "TMA box edges are limited to 256 elements");
     static_assert(NT <= 1024, "too many threads");
     static_assert(MB * (SMEM + 1024) <= 228 * 1024, "MB blocks do not fit in shared memory");
 };
@@ -62,15 +96,14 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
 template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct FastBlock {
     using L = Lattice<D>;
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
-    using real = float;
-    using real2 = float2;
-    static constexpr int Q = L::Q, NB = L::NB, NAUX = Sh::NAUX, NAP = Sh::NAP;
+    static constexpr int Q = L::Q, NB = L::NB, NA2 = Sh::NA2;
     static constexpr int RX = Sh::RX, RS = Sh::RS, SXB = Sh::SXB, PXB = Sh::PXB, SY = Sh::SY;
+    static constexpr int BSLICE = Sh::BSLICE;
 
     const TmaArgs& ta;
     const StepArgs& a;
     unsigned char* smem;
-    int tid, x0, y0, nx, ny, np, p0, p1, pstride;
+    int tid, x0, y0, nx, ny, np, p0, p1, pstride, Ni;
     bool xlo, xhi, ylo, yhi, edge;
     uint32_t bphase = 0, b_pending = 0;
     bool timed_out = false;  // a wait of this thread gave up
@@ -80,16 +113,21 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     int xo = 0;          // FX: bit e+1 set if source column x - e lies outside [0, nx)
     bool reservoir = false;
 
-    __device__ __forceinline__ FastBlock(const TmaArgs& t, unsigned char* sm) : ta(t), a(t.s), smem(sm) {
+    // Tile (bx, by) over march planes [pp0, pp1); bph carries the phase bits
+    // of the variance-slot barriers from the block's previous segment.
+    __device__ __forceinline__ FastBlock(const TmaArgs& t, unsigned char* sm, int bx, int by, int pp0, int pp1,
+                                         uint32_t bph)
+        : ta(t), a(t.s), smem(sm), bphase(bph) {
         tid = threadIdx.x;
-        x0 = blockIdx.x * TX;
-        y0 = (D == 3) ? blockIdx.y * TY : 0;
+        x0 = bx * TX;
+        y0 = (D == 3) ? by * TY : 0;
         nx = a.nx;
         ny = a.ny;
         np = (D == 3) ? a.nz : a.ny;
         pstride = (D == 3) ? nx * ny : nx;
-        p0 = blockIdx.z * a.chunk;
-        p1 = min(p0 + a.chunk, np);
+        Ni = (int)a.N;
+        p0 = pp0;
+        p1 = pp1;
         xlo = (x0 == 0);
         xhi = (x0 + TX == nx);
         ylo = (D == 3) && (y0 == 0);
@@ -105,13 +143,13 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     __device__ __forceinline__ float* bslot(int bs) const {
         return reinterpret_cast<float*>(smem + bs * Sh::BPITCH);
     }
-    __device__ __forceinline__ real* aux(int q) const {
-        return reinterpret_cast<real*>(smem + Sh::OFF_AUX) + ((q - p0 + 1) & 3) * NAP * RS;
+    __device__ __forceinline__ float2* aux(int q) const {
+        return reinterpret_cast<float2*>(smem + Sh::OFF_AUX) + ((q - p0 + 1) & 3) * NA2 * RS;
     }
     __device__ __forceinline__ uint64_t* bbar() const { return reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR); }
     // site values of plane q for tile site t: component k at [k * NINT + t]
-    __device__ __forceinline__ real* sv(int q) const {
-        return reinterpret_cast<real*>(smem + Sh::OFF_SV) + (q & 1) * Sh::NSV * Sh::NINT + tid;
+    __device__ __forceinline__ float* sv(int q) const {
+        return reinterpret_cast<float*>(smem + Sh::OFF_SV) + (q & 1) * Sh::NSV * Sh::NINT + tid;
     }
     __device__ __forceinline__ int bs_of(int q) const { return (q - (p0 - 2)) % Sh::NBS; }
 
@@ -139,7 +177,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     }
 
     // Pull: df_i = stored deviation of fbar*_i at (x - e_i) (Eq. 49).
-    __device__ __forceinline__ void pull(int q, const int* zs, real* df) const {
+    __device__ __forceinline__ void pull(int q, const int* zs, float* df) const {
         const FS* __restrict__ fin = static_cast<const FS*>(a.fin);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -147,14 +185,24 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             const int m = march(i);
             const int sidx = xs[ex + 1] + ((D == 3) ? ys[ey + 1] : 0) + zs[m + 1];
             if (FX && ex != 0 && (xo & (1 << (ex + 1)))) {
-                const real* __restrict__ gf = static_cast<const real*>(a.gf);
-                const long long row = (D == 3) ? (long long)wrap(gyw - ey, ny) + (long long)ny * wrapq(q - ez)
-                                               : (long long)wrapq(q - ey);
-                df[i] = gf[((long long)(ex > 0 ? 0 : 1) * Q + i) * a.rows + row];
+                const float* __restrict__ gf = static_cast<const float*>(a.gf);
+                const int row = (D == 3) ? wrap(gyw - ey, ny) + ny * wrapq(q - ez) : wrapq(q - ey);
+                df[i] = gf[((ex > 0 ? 0 : 1) * Q + i) * (int)a.rows + row];
             } else {
-                df[i] = Store<FS>::ld(fin, (long long)i * a.N + sidx);
+                df[i] = Store<FS>::ld(fin + i * Ni, sidx);
             }
         }
+    }
+
+    // L2 prefetch of the stored populations of march plane P (all Q planes,
+    // the x and y range the tile and its ring pull from).  The first pull
+    // from plane P is made by stage 1 of plane P - 1.
+    __device__ __forceinline__ void prefetch_f(int P) const {
+        constexpr int PXF = 16 / (int)sizeof(FS);
+        if (D == 3)
+            tma_prefetch_l2_4d(&ta.fmap, x0 - PXF, y0 - 2, wrapq(P), 0);
+        else
+            tma_prefetch_l2_3d(&ta.fmap, x0 - PXF, wrapq(P), 0);
     }
 
     // ---- variance copies (thread 0 issues; every thread waits itself) --------
@@ -162,8 +210,8 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         const int bs = bs_of(q);
         mbar_arrive_expect_tx(bbar() + bs, Sh::BBYTES);
         const int plane = wrapq(q);
-        if (D == 3)
-            tma_load_4d(bslot(bs), &ta.bmap, bbar() + bs, x0 - PXB, y0 - 2, plane, 0);
+        if (D == 3)  // pair planes: x in floats of the (2 nx)-wide pair rows
+            tma_load_4d(bslot(bs), &ta.bmap, bbar() + bs, 2 * (x0 - PXB), y0 - 2, plane, 0);
         else
             tma_load_3d(bslot(bs), &ta.bmap, bbar() + bs, x0 - PXB, plane, 0);
     }
@@ -208,7 +256,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     }
     __device__ __forceinline__ void patch_b(int q) {
         const float* __restrict__ bin = static_cast<const float*>(a.bin);
-        const real* __restrict__ gb = static_cast<const real*>(a.gb);
+        const float* __restrict__ gb = static_cast<const float*>(a.gb);
         float* slot = bslot(bs_of(q));
         const int plane = wrapq(q);
         const int cnt = halo_count();
@@ -218,55 +266,120 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             const int sx = gx - (x0 - PXB), sy = (D == 3) ? gy - (y0 - 2) : 0;
             const int wy = (D == 3) ? wrap(gy, ny) : plane;
             const int wx = wrap(gx, nx);
-            const long long row = (D == 3) ? wy + (long long)ny * plane : plane;
-            const long long s = (D == 3) ? wx + (long long)nx * row : wx + (long long)nx * plane;
+            const int row = (D == 3) ? wy + ny * plane : plane;
+            const int s = wx + nx * row;
             const bool res = FX && (gx < 0 || gx >= nx);
+            float v[NB];
 #pragma unroll
             for (int k2 = 0; k2 < NB; ++k2)
-                slot[k2 * Sh::BSLICE + sy * SXB + sx] =
-                    res ? gb[((long long)(gx < 0 ? 0 : 1) * NB + k2) * a.rows + row] : bin[(long long)k2 * a.N + s];
+                v[k2] = res ? gb[((gx < 0 ? 0 : 1) * NB + k2) * (int)a.rows + row]
+                            : bin[BLayout<D, FS>::at(k2, s, Ni)];
+            if (D == 3) {
+                float2* s2 = reinterpret_cast<float2*>(slot) + sy * SXB + sx;
+#pragma unroll
+                for (int p = 0; p < NB / 2; ++p) s2[p * BSLICE] = make_float2(v[2 * p], v[2 * p + 1]);
+            } else {
+#pragma unroll
+                for (int k2 = 0; k2 < NB; ++k2) slot[k2 * BSLICE + sx] = v[k2];
+            }
         }
         fence_proxy_async_smem();  // the slot is refilled by a bulk copy later
     }
 
+    // (u0, rho b) of one site as the float2 groups of the aux slots:
+    //   3D: (u_x, u_y), (rb_xx, rb_xy), (rb_xy, rb_yy), (rb_xz, rb_yz), (u_z, rb_zz)
+    //   2D: (u_x, u_y), (rb_xx, rb_xy), (rb_xy, rb_yy)
+    static __device__ __forceinline__ void put_aux(float2* ax, const float* u0, const float* rb) {
+        if constexpr (D == 3) {
+            ax[0] = make_float2(u0[0], u0[1]);
+            ax[1] = make_float2(rb[0], rb[3]);
+            ax[2] = make_float2(rb[3], rb[1]);
+            ax[3] = make_float2(rb[4], rb[5]);
+            ax[4] = make_float2(u0[2], rb[2]);
+        } else {
+            ax[0] = make_float2(u0[0], u0[1]);
+            ax[1] = make_float2(rb[0], rb[2]);
+            ax[2] = make_float2(rb[2], rb[1]);
+        }
+    }
+
     // ---- stage 1: pull + moments of this thread's region site at plane q -------
-    // Writes (u0, rho b) to the aux plane q; returns the site values for a tile
+    // Writes (u0, rho b) to the aux plane q; keeps the site values for a tile
     // site.  A fixed-state reservoir site writes the reservoir's aux instead.
     __device__ __forceinline__ void stage1(int q, const int* zs, bool tile) {
-        real* ax = aux(q) + (rx + RX * ry) * NAP;
+        float2* ax = aux(q) + (rx + RX * ry) * NA2;
         if (FX && reservoir) {
-            const real* __restrict__ gaux = static_cast<const real*>(a.gaux);
+            const float* __restrict__ gaux = static_cast<const float*>(a.gaux);
             const int qq = wrapq(q);
-            const long long row = (D == 3) ? gyw + (long long)ny * qq : qq;
+            const int row = (D == 3) ? gyw + ny * qq : qq;
             const int side = (x0 - 1 + rx) < 0 ? 0 : 1;
+            constexpr int NAUX = D + NB;
+            float u0[D], rb[NB];
 #pragma unroll
-            for (int k = 0; k < NAUX; ++k) ax[k] = gaux[((long long)side * NAUX + k) * a.rows + row];
+            for (int c = 0; c < D; ++c) u0[c] = gaux[(side * NAUX + c) * (int)a.rows + row];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) rb[k] = gaux[(side * NAUX + D + k) * (int)a.rows + row];
+            put_aux(ax, u0, rb);
             return;
         }
-        real df[Q];
+        float df[Q];
         pull(q, zs, df);
         const int bo = ((D == 3) ? (ry + 1) * SXB : 0) + (rx - 1 + PXB);
-        const float* bm = bslot(bs_of(q - 1)) + bo;
-        const float* b0 = bslot(bs_of(q)) + bo;
-        const float* bp = bslot(bs_of(q + 1)) + bo;
-        real bsum[NB];
+        float bsum[NB];
+        if constexpr (D == 3) {
+            // pairs (xx, yy), (zz, xy), (xz, yz), packed multiply-adds
+            const float2* bm = reinterpret_cast<const float2*>(bslot(bs_of(q - 1))) + bo;
+            const float2* b0 = reinterpret_cast<const float2*>(bslot(bs_of(q))) + bo;
+            const float2* bp = reinterpret_cast<const float2*>(bslot(bs_of(q + 1))) + bo;
+            float2 acc[3];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
+            for (int i = 0; i < Q; ++i) {
+                const int offb = -L::e(i, 1) * SXB - L::e(i, 0);
+                const int m = march(i);
+                const float2* src = ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
+                const float fi = float(L::w(i)) + df[i];
+                const float2 f2 = make_float2(fi, fi);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int offb = (D == 3) ? -L::e(i, 1) * SXB - L::e(i, 0) : -L::e(i, 0);
-            const int m = march(i);
-            const float* bsrc = (m == 1) ? bm : ((m == -1) ? bp : b0);
-            const real fi = real(L::w(i)) + df[i];
+                for (int p = 0; p < 3; ++p)
+                    acc[p] = (i == 0) ? __fmul2_rn(f2, src[p * BSLICE]) : __ffma2_rn(f2, src[p * BSLICE], acc[p]);
+            }
 #pragma unroll
-            for (int k = 0; k < NB; ++k) bsum[k] += fi * bsrc[k * Sh::BSLICE + offb];
+            for (int p = 0; p < 3; ++p) {
+                bsum[2 * p] = acc[p].x;
+                bsum[2 * p + 1] = acc[p].y;
+            }
+        } else {
+            const float* bm = bslot(bs_of(q - 1)) + bo;
+            const float* b0 = bslot(bs_of(q)) + bo;
+            const float* bp = bslot(bs_of(q + 1)) + bo;
+            float2 acc2;
+            float accxy;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int offb = -L::e(i, 0);
+                const int m = march(i);
+                const float* src = ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
+                const float fi = float(L::w(i)) + df[i];
+                const float2 f2 = make_float2(fi, fi);
+                const float2 bxy = make_float2(src[0], src[BSLICE]);
+                if (i == 0) {
+                    acc2 = __fmul2_rn(f2, bxy);
+                    accxy = fi * src[2 * BSLICE];
+                } else {
+                    acc2 = __ffma2_rn(f2, bxy, acc2);
+                    accxy = fmaf(fi, src[2 * BSLICE], accxy);
+                }
+            }
+            bsum[0] = acc2.x;
+            bsum[1] = acc2.y;
+            bsum[2] = accxy;
         }
-        real u0[D], rb[NB], bt[NB], rho, j[D], E;
-        real omega, tau, T0;
+        float u0[D], rb[NB], bt[NB], rho, j[D], E;
+        float omega, tau, T0;
         step_params(a, omega, tau, T0);
-        site_moments<D, real>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
+        site_moments<D, float>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
         if (tile) {
-            real* v = sv(q);
+            float* v = sv(q);
             constexpr int NI = Sh::NINT;
 #pragma unroll
             for (int k = 0; k < NB; ++k) v[k * NI] = bt[k];
@@ -275,77 +388,150 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             for (int c = 0; c < D; ++c) v[(NB + 1 + c) * NI] = j[c];
             v[(NB + 1 + D) * NI] = E;
         }
-        real vals[NAP];
-#pragma unroll
-        for (int c = 0; c < D; ++c) vals[c] = u0[c];
-#pragma unroll
-        for (int k = 0; k < NB; ++k) vals[D + k] = rb[k];
-        if (NAP > NAUX) vals[NAP - 1] = real(0);
-        real2* dst = reinterpret_cast<real2*>(ax);
-#pragma unroll
-        for (int k = 0; k < NAP / 2; ++k) dst[k] = make_float2(vals[2 * k], vals[2 * k + 1]);
+        put_aux(ax, u0, rb);
+    }
+
+    // Gradient contribution of neighbour x + e_i (unscaled, sign of e_i folded
+    // in): v = e_i . (rho b); F += v; G_bc += u_c v_b + u_b v_c, the diagonal
+    // counted once (doubled at the end).  `n` points at the neighbour's aux.
+    template <int I>
+    static __device__ __forceinline__ void grad_term(const float2* n, float* F, float* G) {
+        constexpr int ex = L::e(I, 0), ey = L::e(I, 1), ez = L::e(I, 2);
+        const float2 A0 = n[0];
+        if constexpr (D == 3) {
+            const float2 A3 = n[3], A4 = n[4];
+            const float ux = A0.x, uy = A0.y, uz = A4.x;
+            float vx = 0.0f, vy = 0.0f, vz = 0.0f;
+            bool first = true;
+            auto addrow = [&](int s, float rx_, float ry_, float rz_) {
+                if (first) {
+                    vx = s * rx_;
+                    vy = s * ry_;
+                    vz = s * rz_;
+                    first = false;
+                } else {
+                    vx += s * rx_;
+                    vy += s * ry_;
+                    vz += s * rz_;
+                }
+            };
+            if constexpr (ex != 0) {
+                const float2 A1 = n[1];
+                addrow(ex, A1.x, A1.y, A3.x);  // row x: (xx, xy, xz)
+            }
+            if constexpr (ey != 0) {
+                const float2 A2 = n[2];
+                addrow(ey, A2.x, A2.y, A3.y);  // row y: (xy, yy, yz)
+            }
+            if constexpr (ez != 0) addrow(ez, A3.x, A3.y, A4.y);  // row z: (xz, yz, zz)
+            F[0] += vx;
+            F[1] += vy;
+            F[2] += vz;
+            G[0] = fmaf(ux, vx, G[0]);
+            G[1] = fmaf(uy, vy, G[1]);
+            G[2] = fmaf(uz, vz, G[2]);
+            G[3] = fmaf(uy, vx, fmaf(ux, vy, G[3]));
+            G[4] = fmaf(uz, vx, fmaf(ux, vz, G[4]));
+            G[5] = fmaf(uz, vy, fmaf(uy, vz, G[5]));
+        } else {
+            const float ux = A0.x, uy = A0.y;
+            float vx = 0.0f, vy = 0.0f;
+            if constexpr (ex != 0) {
+                const float2 A1 = n[1];
+                vx = ex * A1.x;
+                vy = ex * A1.y;
+            }
+            if constexpr (ey != 0) {
+                const float2 A2 = n[2];
+                if constexpr (ex != 0) {
+                    vx += ey * A2.x;
+                    vy += ey * A2.y;
+                } else {
+                    vx = ey * A2.x;
+                    vy = ey * A2.y;
+                }
+            }
+            F[0] += vx;
+            F[1] += vy;
+            G[0] = fmaf(ux, vx, G[0]);
+            G[1] = fmaf(uy, vy, G[1]);
+            G[2] = fmaf(uy, vx, fmaf(ux, vy, G[2]));
+        }
+    }
+
+    template <int I>
+    __device__ __forceinline__ void grad_at(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
+                                            float* G) const {
+        constexpr int m = (D == 3) ? L::e(I, 2) : L::e(I, 1);
+        const float2* as = (m == 1) ? ap : ((m == -1) ? am : a0);
+        constexpr int r = L::e(I, 0) + ((D == 3) ? RX * L::e(I, 1) : 0);
+        grad_term<I>(as + (rc + r) * NA2, F, G);
+    }
+
+    template <int... Is>
+    __device__ __forceinline__ void grad_axes(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
+                                              float* G, std::integer_sequence<int, Is...>) const {
+        ((norm2<D>(Is + 1) == 1 ? grad_at<Is + 1>(am, a0, ap, rc, F, G) : void()), ...);
+    }
+    template <int... Is>
+    __device__ __forceinline__ void grad_edges(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
+                                               float* G, std::integer_sequence<int, Is...>) const {
+        ((norm2<D>(Is + 1) == 2 ? grad_at<Is + 1>(am, a0, ap, rc, F, G) : void()), ...);
     }
 
     // ---- stage 2: gradients, collision and store of this tile site at plane p ----
-    __device__ __forceinline__ void stage2(int p, const int* zsp, DiagAcc<real, D + 2>& acc, int& bad) {
-        const long long s = (long long)xs[1] + ((D == 3) ? ys[1] : 0) + zsp[1];
-        const int rc = (rx + RX * ry) * NAP;
-        const real* am = aux(p - 1) + rc;
-        const real* a0 = aux(p) + rc;
-        const real* ap = aux(p + 1) + rc;
-        real F[D], G[NB];
+    __device__ __forceinline__ void stage2(int p, const int* zsp, DiagDev<D + 2>& acc, int& bad) {
+        const int s = xs[1] + ((D == 3) ? ys[1] : 0) + zsp[1];
+        const int rc = rx + RX * ry;
+        const float2* am = aux(p - 1);
+        const float2* a0 = aux(p);
+        const float2* ap = aux(p + 1);
+        float F[D], G[NB];
 #pragma unroll
-        for (int c = 0; c < D; ++c) F[c] = real(-0.0);
+        for (int c = 0; c < D; ++c) F[c] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] = real(-0.0);
+        for (int k = 0; k < NB; ++k) G[k] = 0.0f;
+        // F = -3 sum_i w_i v_i, G = -3 sum_i w_i (u v + v u): the axis terms
+        // carry w_axis = (w_axis / w_edge) w_edge, so sum them first, scale by
+        // that ratio (2 on D3Q19, 4 on D2Q9), then add the edge terms and
+        // scale everything by -3 w_edge (diagonal of G: twice that).
+        grad_axes(am, a0, ap, rc, F, G, std::make_integer_sequence<int, Q - 1>{});
+        constexpr float ratio = float(L::w(1) / L::w(Q - 1));
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int m = march(i);
-            const real* as = (m == 1) ? ap : ((m == -1) ? am : a0);
-            const int r = L::e(i, 0) + ((D == 3) ? RX * L::e(i, 1) : 0);
-            const real2* src = reinterpret_cast<const real2*>(as + r * NAP);
-            real vals[NAP];
+        for (int c = 0; c < D; ++c) F[c] *= ratio;
 #pragma unroll
-            for (int k = 0; k < NAP / 2; ++k) {
-                const real2 v2 = src[k];
-                vals[2 * k] = v2.x;
-                vals[2 * k + 1] = v2.y;
-            }
-            fd_add<D, real>(i, vals + D, vals, F, G);
-        }
+        for (int k = 0; k < NB; ++k) G[k] *= ratio;
+        grad_edges(am, a0, ap, rc, F, G, std::make_integer_sequence<int, Q - 1>{});
+        constexpr float sc = float(-3.0 * L::w(Q - 1));
 #pragma unroll
-        for (int c = 0; c < D; ++c) F[c] *= real(-3);
+        for (int c = 0; c < D; ++c) F[c] *= sc;
 #pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] *= real(-3);
-        const real* v = sv(p);
+        for (int k = 0; k < NB; ++k) G[k] *= (k < D ? 2.0f * sc : sc);
+        const float* v = sv(p);
         constexpr int NI = Sh::NINT;
-        real c_bt[NB], c_j[D];
+        float c_bt[NB], c_j[D];
 #pragma unroll
         for (int k = 0; k < NB; ++k) c_bt[k] = v[k * NI];
-        const real c_rho = v[NB * NI];
+        const float c_rho = v[NB * NI];
 #pragma unroll
         for (int c = 0; c < D; ++c) c_j[c] = v[(NB + 1 + c) * NI];
-        const real c_E = v[(NB + 1 + D) * NI];
-        real df[Q];
-        pull(p, zsp, df);  // second pull of the same values: cache hits
-        site_collide<D, FS, real>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
+        const float c_E = v[(NB + 1 + D) * NI];
+        float df[Q];
+        pull(p, zsp, df);  // second pull of the same values
+        site_collide<D, FS, float, int, DiagDev<D + 2>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     }
 };
 
+// One segment of the march: tile (bx, by), planes [p0, p1).  Returns false
+// if a wait for a variance copy gave up (the block's copies in flight are
+// drained and the error flag raised; the caller leaves the kernel).
 template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX>
-__global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
-    step_fast_kernel(const __grid_constant__ TmaArgs ta) {
+__device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* smem, int bx, int by, int p0,
+                                             int p1, DiagDev<D + 2>& acc, int& bad, uint32_t& bphase) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
-    constexpr int NINT = Sh::NINT, NRING = Sh::NRING, NT = Sh::NT, RX = Sh::RX;
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    FastBlock<D, FS, TX, TY, PFB, MB, FX> blk(ta, smem);
+    constexpr int NINT = Sh::NINT, NRING = Sh::NRING, RX = Sh::RX;
+    FastBlock<D, FS, TX, TY, PFB, MB, FX> blk(ta, smem, bx, by, p0, p1, bphase);
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int k = 0; k < Sh::NBS; ++k) mbar_init(blk.bbar() + k, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
 
     // role of this thread: tile site (stage 1 + stage 2), ring site (stage 1)
     // or idle padding of the last warp
@@ -373,15 +559,15 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
     }
     blk.set_site(rx, ry);
 
-    DiagAcc<float, D + 2> acc;
-    int bad = 0;
-
-    const int p0 = blk.p0, p1 = blk.p1;
     // prologue: variance planes p0-2 .. p0+PFB (the slots' first fill)
+    if (tid == 0) fence_proxy_async_smem();  // slots may hold generic-proxy halo writes of a previous segment
     for (int q = p0 - 2; q <= min(p0 + PFB, p1 + 1); ++q) {
         if (tid == 0) blk.issue_b(q);
         blk.b_pending |= 1u << blk.bs_of(q);
     }
+    // populations of the first planes the pulls read (p0-2 .. p0+2) into L2
+    if (tid == 0)
+        for (int P = p0 - 2; P <= min(p0 + 2, p1 + 1); ++P) blk.prefetch_f(P);
     blk.wait_b(p0 - 2);
     blk.wait_b(p0 - 1);
     if (blk.edge) {
@@ -389,7 +575,6 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
         blk.patch_b(p0 - 1);
     }
     int zs[3], zsp[3] = {0, 0, 0};
-    bool aborted = false;
     for (int q = p0 - 1; q <= p1; ++q) {
         blk.wait_b(q + 1);
         if (blk.edge) {
@@ -402,8 +587,12 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
         // of the variance slot of plane q-1 is done.  It also tells every
         // thread at once whether any wait gave up, so all leave together.
         if (__syncthreads_or(blk.timed_out)) {
-            aborted = true;
-            break;
+            // drain this block's copies still in flight, then leave
+            if (tid == 0) {
+                atomicOr(ta.s.flag, 4);
+                blk.drain();
+            }
+            return false;
         }
         const int qn = q + 2 + PFB;
         if (qn <= p1 + 1) {
@@ -413,21 +602,63 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
             }
             blk.b_pending |= 1u << blk.bs_of(qn);
         }
+        // populations two planes ahead of the next stage 1
+        if (tid == 0 && q + 3 <= p1 + 1) blk.prefetch_f(q + 3);
         if (interior && q - 1 >= p0) blk.stage2(q - 1, zsp, acc, bad);
 #pragma unroll
         for (int e = 0; e < 3; ++e) zsp[e] = zs[e];
     }
-    if (aborted) {
-        // drain this block's copies still in flight, then leave
-        if (tid == 0) {
-            atomicOr(ta.s.flag, 4);
-            blk.drain();
-        }
-        return;
+    bphase = blk.bphase;
+    // the next segment rewrites the aux and site-value slots
+    __syncthreads();
+    return true;
+}
+
+// Grid: (nx/TX, ny/TY, chunks) with one segment per block, or, with PERSIST,
+// a one-dimensional grid of about the resident block count in which block b
+// takes the b-th equal share of the (tile column, plane) work in column-major
+// order -- a contiguous run of planes of one or two columns -- so that the
+// load is balanced without a tail wave and each block restarts its march at
+// most once or twice.
+template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX, bool PERSIST>
+__global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
+    step_fast_kernel(const __grid_constant__ TmaArgs ta) {
+    using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
+    if (tid == 0) {
+        for (int k = 0; k < Sh::NBS; ++k) mbar_init(bars + k, 1);
+        fence_barrier_init();
     }
+    __syncthreads();
+
+    DiagDev<D + 2> acc(float(D) * ta.s.T0_f);
+    int bad = 0;
+    uint32_t bphase = 0;
+    bool ok = true;
+    if constexpr (PERSIST) {
+        const int np = (D == 3) ? ta.s.nz : ta.s.ny;
+        const int ncx = ta.s.nx / TX;
+        const long long W = (long long)ncx * ((D == 3) ? ta.s.ny / TY : 1) * np;
+        const long long w1 = W * (blockIdx.x + 1) / gridDim.x;
+        for (long long w = W * blockIdx.x / gridDim.x; ok && w < w1;) {
+            const int col = (int)(w / np);
+            const int p0 = (int)(w - (long long)col * np);
+            const int p1 = (int)min((long long)np, p0 + (w1 - w));
+            ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, col % ncx, col / ncx, p0, p1, acc, bad, bphase);
+            w += p1 - p0;
+        }
+    } else {
+        const int np = (D == 3) ? ta.s.nz : ta.s.ny;
+        const int p0 = blockIdx.z * ta.s.chunk;
+        ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, blockIdx.x, blockIdx.y, p0,
+                                                       min(p0 + ta.s.chunk, np), acc, bad, bphase);
+    }
+    if (!ok) return;
     if (bad) atomicOr(ta.s.flag, bad);
     if (ta.s.want_diag)
-        block_diagnostics<D, NT>(ta.s, acc, reinterpret_cast<double*>(smem + Sh::OFF_RED));
+        block_diagnostics<D, Sh::NT>(ta.s, acc, reinterpret_cast<double*>(smem + Sh::OFF_RED));
 }
 
 }  // namespace lbm

@@ -83,10 +83,27 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Bulk tensor prefetch global -> L2 of one box (no shared memory, no barrier):
+// later loads of the box hit in L2.  Out-of-bounds parts of the box are
+// ignored.
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_l2_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
 // Arguments of the TMA-staged kernel: the generic step arguments plus the
 // tensor maps of the input buffer (populations and variance planes).
 struct TmaArgs {
-    CUtensorMap fmap;  // populations: (nx, ny[, nz], Q), storage type
+    CUtensorMap fmap;  // populations: (nx, ny[, nz], Q), storage type; box of all Q planes
     CUtensorMap bmap;  // variance:    (nx, ny[, nz], NB), breal
     StepArgs s;
 };

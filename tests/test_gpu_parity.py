@@ -369,3 +369,35 @@ def test_staged_variants_match_generic(d, shape, ntma, bc, dtype):
             if bc == "periodic":
                 wf, wb = check_windows(d, f0, b0, f1, b1, tau, T0, thermal, n_windows=3, half=4)
                 assert wf < (2e-6 if dtype == "f32" else 2e-3) and wb < 2e-6
+
+
+@pytest.mark.parametrize("d,shape", [(3, (32, 32, 64)), (2, (1, 64, 256))])
+def test_fp32_diagnostics_match_exact_state_sums(d, shape):
+    """The staged kernel sums the diagnostics per thread in FP32 as
+    deviations from the rest state.  The mass of a state is the sum of all
+    stored populations (the pull is a permutation), and the momentum that sum
+    weighted by e_i plus half the summed gradient correction, which vanishes
+    on a periodic lattice up to FP32 rounding of the antisymmetric sums.
+    Checked against FP64 sums of the stored FP32 state: the only error left is
+    the FP32 rounding of each site's rho and j."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(11)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((d,) + shape)
+    T = 0.1 * (1 + 0.05 * rng.random(shape))
+    for k in range(4):
+        g = lbm.Simulation(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True, dtype="f32",
+                           tile=TMA_BASE + k, chunk=8)
+        g.init(rho, u, T)
+        g.step(5)
+        f, _ = g.emitted()
+        diag = g.diagnostics()
+        mass = f.sum()
+        # per site the kernel's rho is an FP32 number near 1 (rounding <= 2^-24);
+        # summed over N sites the error grows like sqrt(N) 2^-24: 1e-9 relative
+        # is four standard deviations at N = 65536
+        assert abs(diag[0] - mass) / mass < 1e-9
+        e, _ = oracle.lattice(d)  # velocity order of the emitted planes
+        mom = np.array([(e[:, a].reshape((-1,) + (1,) * (f.ndim - 1)) * f).sum() for a in range(d)])
+        assert np.abs(diag[1:1 + d] - mom).max() / mass < 1e-8
+        g.close()
