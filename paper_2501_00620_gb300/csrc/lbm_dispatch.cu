@@ -40,7 +40,10 @@ int device_sms() {
 
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
 
-const char* kernel_name(int D, int v) { return v < kTmaBase ? "step_kernel" : "step_fast_kernel"; }
+const char* kernel_name(int D, int v) {
+    if (v >= kTmaBase) return "step_fast_kernel";
+    return (D == 2 && v == 3) ? "step_strip_kernel" : "step_kernel";
+}
 
 int n_tma_variants(int D) { return D == 2 ? n_fast_variants_d2() : (D == 3 ? n_fast_variants_d3() : 0); }
 

@@ -15,6 +15,10 @@ struct Variant {
     int tx, ty;
 };
 
+// Threads per block of the D2Q9 strip kernel (lbm_step_strip.cuh): NT - 2
+// tile sites per strip.
+constexpr int kStripNT = 256;
+
 // Variant indices: 0..n_variants(D)-1 select the generic kernel's tiles;
 // kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;

@@ -1,11 +1,14 @@
 // Launchers for the D2 lattice (tile variants x storage types).
 #include "lbm_internal.h"
+#include "lbm_step_strip.cuh"
 
 namespace lbm {
 
 namespace {
 constexpr int kD = 2;
-constexpr Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}};
+// 0-2: generic kernel strips; 3: strip kernel (lbm_step_strip.cuh), 254 sites
+// per 256-thread block, FP32/16-bit storage.
+constexpr Variant kVariants[] = {{256, 1}, {128, 1}, {512, 1}, {kStripNT - 2, 1}};
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <typename FS, int TX, int TY>
@@ -25,12 +28,38 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename FS, bool FX>
+cudaError_t launch_strip_fx(const StepArgs& a, cudaStream_t st) {
+    using Sh = StripShape<FS, kStripNT>;
+    auto kern = step_strip_kernel<FS, kStripNT, FX>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.nx + Sh::TX - 1) / Sh::TX, 1, (a.ny + a.chunk - 1) / a.chunk);
+    kern<<<grid, kStripNT, Sh::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename FS>
+cudaError_t launch_strip(const StepArgs& a, cudaStream_t st) {
+    if constexpr (std::is_same<FS, double>::value) {
+        return cudaErrorInvalidValue;  // FP32 arithmetic only
+    } else {
+        if (a.N >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit site indices
+        return a.fixed_x ? launch_strip_fx<FS, true>(a, st) : launch_strip_fx<FS, false>(a, st);
+    }
+}
+
 template <typename FS>
 cudaError_t launch_dtype(int v, const StepArgs& a, cudaStream_t st) {
     switch (v) {
         case 0: return launch_one<FS, 256, 1>(a, st);
         case 1: return launch_one<FS, 128, 1>(a, st);
         case 2: return launch_one<FS, 512, 1>(a, st);
+        case 3: return launch_strip<FS>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -41,6 +70,7 @@ size_t smem_of(int v) {
         case 0: return StepShape<kD, FS, 256, 1>::smem;
         case 1: return StepShape<kD, FS, 128, 1>::smem;
         case 2: return StepShape<kD, FS, 512, 1>::smem;
+        case 3: return StripShape<FS, kStripNT>::SMEM;
         default: return 0;
     }
 }

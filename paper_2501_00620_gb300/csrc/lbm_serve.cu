@@ -1,10 +1,11 @@
 // Continuous-batching service (include/lbm_serve.h): many resident D1Q3 /
 // D2Q9 simulations in FP32 advanced together by one cooperative kernel.
 //
-// Device side: serve_kernel walks a work list of tiles (256-site strips, 2D
-// strips span kChunk2 rows) of every active simulation, running the fused
-// step of the generic kernel (step_block) on each, with a grid-wide barrier
-// between steps; it advances the round's K steps in one launch.  Each
+// Device side: serve_kernel walks a work list of tiles of every active
+// simulation -- 1D: 256-site strips run by the generic kernel's tile body
+// (step_block); 2D: strips of 254 sites x kChunk2 rows run by the strip
+// kernel's body (strip_block, any extent) -- with a grid-wide
+// barrier between steps; it advances the round's K steps in one launch.  Each
 // simulation keeps its own A-B buffers, parity and step budget for the round.
 //
 // Host side: a service thread admits queued requests first come first
@@ -29,6 +30,7 @@
 
 #include "../../include/lbm_serve.h"
 #include "lbm_internal.h"
+#include "lbm_step_strip.cuh"
 
 namespace lbm {
 void set_last_error(const std::string& m);  // lbm_capi.cu
@@ -44,19 +46,21 @@ constexpr int kChunk2 = 16;  // rows per 2D work item
 constexpr size_t kAlign = 256;
 
 struct ServeSim {
-    StepArgs a;  // per-simulation arguments; buffers set per step from f/b
+    StepArgs a[2];  // per-simulation arguments for input buffer 0 and 1
     void* f[2];
     void* b[2];
     int d, tiles_x, item0, steps, cur;
+    int strip;  // 2D: the strip kernel's body
 };
 
 using Sh1 = StepShape<1, float, kTX, 1>;
-using Sh2 = StepShape<2, float, kTX, 1>;
-constexpr size_t kSmem = Sh1::smem > Sh2::smem ? Sh1::smem : Sh2::smem;
+using ShS = StripShape<float, kTX>;
+static_assert(kTX == kStripNT, "the strip body runs on the serve kernel's blocks");
+constexpr size_t kSmem = Sh1::smem > (size_t)ShS::SMEM ? Sh1::smem : (size_t)ShS::SMEM;
 
 // K steps of every simulation in `sims` (sorted by item0); work item `it`
 // belongs to the last simulation with item0 <= it.
-__global__ void __launch_bounds__(kTX) serve_kernel(const ServeSim* __restrict__ sims, int nsims, int nitems,
+__global__ void __launch_bounds__(kTX, 2) serve_kernel(const ServeSim* __restrict__ sims, int nsims, int nitems,
                                                     int K) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::grid_group grid = cg::this_grid();
@@ -72,17 +76,21 @@ __global__ void __launch_bounds__(kTX) serve_kernel(const ServeSim* __restrict__
             }
             const ServeSim& S = sims[lo];
             if (k >= S.steps) continue;  // uniform over the block
-            StepArgs a = S.a;
-            const int par = (S.cur + k) & 1;
-            a.fin = S.f[par];
-            a.bin = S.b[par];
-            a.fout = S.f[par ^ 1];
-            a.bout = S.b[par ^ 1];
+            // read in place (not copied to registers): the tile bodies load
+            // the fields they need
+            const StepArgs& a = S.a[(S.cur + k) & 1];
             const int local = it - S.item0;
-            if (S.d == 1)
+            if (S.d == 1) {
                 step_block<1, float, kTX, 1>(a, local, 0, 0, smem);
-            else
-                step_block<2, float, kTX, 1>(a, local % S.tiles_x, 0, local / S.tiles_x, smem);
+            } else {
+                DiagDev<4> acc(0.0f);  // unused: no diagnostics in serving rounds
+                int bad = 0;
+                if (a.fixed_x)
+                    strip_block<float, kTX, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+                else
+                    strip_block<float, kTX, false>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+                if (bad) atomicOr(a.flag, bad);
+            }
             __syncthreads();  // the next work item reuses shared memory
         }
         grid.sync();
@@ -224,6 +232,9 @@ struct Server {
     void retire(const std::shared_ptr<Request>& r);
 };
 
+// 2D requests run on the strip kernel's tile body.
+bool uses_strip(const Request& r) { return r.d == 2; }
+
 StepArgs sim_args(const Server& S, const Request& r) {
     char* base = S.pool_mem + r.off;
     StepArgs a{};
@@ -281,7 +292,8 @@ void Server::retire(const std::shared_ptr<Request>& r) {
     a.bout = base + r->lay.b[r->cur ^ 1];
     a.write_state = 0;
     a.mout = reinterpret_cast<double*>(base + r->lay.m);
-    cudaError_t e = launch_step(r->d, DT_F32, 0, a, stream);
+    // the same tile body as the steps (strip kernel, variant 3, for 2D)
+    cudaError_t e = launch_step(r->d, DT_F32, uses_strip(*r) ? 3 : 0, a, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(r->fields.data(), a.mout, sizeof(double) * (2 + r->d) * r->N, cudaMemcpyDeviceToHost,
                             stream);
@@ -332,13 +344,20 @@ void Server::loop() {
             const Request& r = *active[i];
             char* base = pool_mem + r.off;
             ServeSim& s = h_sims[i];
-            s.a = sim_args(*this, r);
             for (int k = 0; k < 2; ++k) {
                 s.f[k] = base + r.lay.f[k];
                 s.b[k] = base + r.lay.b[k];
             }
+            for (int k = 0; k < 2; ++k) {
+                s.a[k] = sim_args(*this, r);
+                s.a[k].fin = s.f[k];
+                s.a[k].bin = s.b[k];
+                s.a[k].fout = s.f[k ^ 1];
+                s.a[k].bout = s.b[k ^ 1];
+            }
             s.d = r.d;
-            s.tiles_x = (r.nx + kTX - 1) / kTX;
+            s.strip = uses_strip(r) ? 1 : 0;
+            s.tiles_x = s.strip ? (r.nx + ShS::TX - 1) / ShS::TX : (r.nx + kTX - 1) / kTX;
             s.item0 = items;
             s.steps = (int)std::min(K, r.remaining);
             s.cur = r.cur;
@@ -478,7 +497,9 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         return cleanup(std::string("server set-up: ") + cudaGetErrorString(e));
     S.pool.reset(S.pool_mem, o.hbm_budget);
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kTX, kSmem);
+    // the strip body needs more than the default 48 KB of dynamic shared memory
+    e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kTX, kSmem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
     if (e != cudaSuccess || per_sm < 1) return cleanup("serve kernel occupancy query failed");
     S.grid_max = per_sm * sms;

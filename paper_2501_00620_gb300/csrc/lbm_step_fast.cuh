@@ -34,36 +34,10 @@
 
 #include <utility>
 
-#include "lbm_site.cuh"
+#include "lbm_lean.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
-
-// FP32 accumulator of the conservation diagnostics (mass, momentum, energy)
-// as deviations from the rest state: mass as rho - 1, energy as E - eref with
-// eref = D T0.  get() adds the references back in FP64.
-template <int K> struct DiagDev {
-    float d[K];
-    int n;
-    float eref;
-    __device__ __forceinline__ explicit DiagDev(float e) : n(0), eref(e) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) d[k] = 0.0f;
-    }
-    __device__ __forceinline__ void add(int k, float x) {
-        if (k == 0) {
-            d[0] += x - 1.0f;
-            ++n;
-        } else if (k == K - 1) {
-            d[k] += x - eref;
-        } else {
-            d[k] += x;
-        }
-    }
-    __device__ __forceinline__ double get(int k) const {
-        return double(d[k]) + (k == 0 ? double(n) : (k == K - 1 ? double(n) * double(eref) : 0.0));
-    }
-};
 
 template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape {
     using L = Lattice<D>;
@@ -286,23 +260,6 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         fence_proxy_async_smem();  // the slot is refilled by a bulk copy later
     }
 
-    // (u0, rho b) of one site as the float2 groups of the aux slots:
-    //   3D: (u_x, u_y), (rb_xx, rb_xy), (rb_xy, rb_yy), (rb_xz, rb_yz), (u_z, rb_zz)
-    //   2D: (u_x, u_y), (rb_xx, rb_xy), (rb_xy, rb_yy)
-    static __device__ __forceinline__ void put_aux(float2* ax, const float* u0, const float* rb) {
-        if constexpr (D == 3) {
-            ax[0] = make_float2(u0[0], u0[1]);
-            ax[1] = make_float2(rb[0], rb[3]);
-            ax[2] = make_float2(rb[3], rb[1]);
-            ax[3] = make_float2(rb[4], rb[5]);
-            ax[4] = make_float2(u0[2], rb[2]);
-        } else {
-            ax[0] = make_float2(u0[0], u0[1]);
-            ax[1] = make_float2(rb[0], rb[2]);
-            ax[2] = make_float2(rb[2], rb[1]);
-        }
-    }
-
     // ---- stage 1: pull + moments of this thread's region site at plane q -------
     // Writes (u0, rho b) to the aux plane q; keeps the site values for a tile
     // site.  A fixed-state reservoir site writes the reservoir's aux instead.
@@ -319,7 +276,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             for (int c = 0; c < D; ++c) u0[c] = gaux[(side * NAUX + c) * (int)a.rows + row];
 #pragma unroll
             for (int k = 0; k < NB; ++k) rb[k] = gaux[(side * NAUX + D + k) * (int)a.rows + row];
-            put_aux(ax, u0, rb);
+            put_aux<D>(ax, u0, rb);
             return;
         }
         float df[Q];
@@ -328,25 +285,32 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         float bsum[NB];
         if constexpr (D == 3) {
             // pairs (xx, yy), (zz, xy), (xz, yz), packed multiply-adds
-            const float2* bm = reinterpret_cast<const float2*>(bslot(bs_of(q - 1))) + bo;
-            const float2* b0 = reinterpret_cast<const float2*>(bslot(bs_of(q))) + bo;
-            const float2* bp = reinterpret_cast<const float2*>(bslot(bs_of(q + 1))) + bo;
-            float2 acc[3];
+            const int s0 = bs_of(q);
+            const int sm = s0 == 0 ? Sh::NBS - 1 : s0 - 1, sp = s0 == Sh::NBS - 1 ? 0 : s0 + 1;
+            const float2* bm = reinterpret_cast<const float2*>(bslot(sm)) + bo;
+            const float2* b0 = reinterpret_cast<const float2*>(bslot(s0)) + bo;
+            const float2* bp = reinterpret_cast<const float2*>(bslot(sp)) + bo;
+            // two independent accumulator sets (in-plane sources, off-plane
+            // sources) halve the dependency chains of the multiply-adds
+            float2 acc[2][3];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int offb = -L::e(i, 1) * SXB - L::e(i, 0);
                 const int m = march(i);
+                const int h = (m == 0) ? 0 : 1;
+                const bool first = (i == 0) || (i == 5);  // first in-plane / off-plane source
                 const float2* src = ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
                 const float fi = float(L::w(i)) + df[i];
                 const float2 f2 = make_float2(fi, fi);
 #pragma unroll
                 for (int p = 0; p < 3; ++p)
-                    acc[p] = (i == 0) ? __fmul2_rn(f2, src[p * BSLICE]) : __ffma2_rn(f2, src[p * BSLICE], acc[p]);
+                    acc[h][p] = first ? __fmul2_rn(f2, src[p * BSLICE]) : __ffma2_rn(f2, src[p * BSLICE], acc[h][p]);
             }
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                bsum[2 * p] = acc[p].x;
-                bsum[2 * p + 1] = acc[p].y;
+                const float2 t = __fadd2_rn(acc[0][p], acc[1][p]);
+                bsum[2 * p] = t.x;
+                bsum[2 * p + 1] = t.y;
             }
         } else {
             const float* bm = bslot(bs_of(q - 1)) + bo;
@@ -388,75 +352,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             for (int c = 0; c < D; ++c) v[(NB + 1 + c) * NI] = j[c];
             v[(NB + 1 + D) * NI] = E;
         }
-        put_aux(ax, u0, rb);
-    }
-
-    // Gradient contribution of neighbour x + e_i (unscaled, sign of e_i folded
-    // in): v = e_i . (rho b); F += v; G_bc += u_c v_b + u_b v_c, the diagonal
-    // counted once (doubled at the end).  `n` points at the neighbour's aux.
-    template <int I>
-    static __device__ __forceinline__ void grad_term(const float2* n, float* F, float* G) {
-        constexpr int ex = L::e(I, 0), ey = L::e(I, 1), ez = L::e(I, 2);
-        const float2 A0 = n[0];
-        if constexpr (D == 3) {
-            const float2 A3 = n[3], A4 = n[4];
-            const float ux = A0.x, uy = A0.y, uz = A4.x;
-            float vx = 0.0f, vy = 0.0f, vz = 0.0f;
-            bool first = true;
-            auto addrow = [&](int s, float rx_, float ry_, float rz_) {
-                if (first) {
-                    vx = s * rx_;
-                    vy = s * ry_;
-                    vz = s * rz_;
-                    first = false;
-                } else {
-                    vx += s * rx_;
-                    vy += s * ry_;
-                    vz += s * rz_;
-                }
-            };
-            if constexpr (ex != 0) {
-                const float2 A1 = n[1];
-                addrow(ex, A1.x, A1.y, A3.x);  // row x: (xx, xy, xz)
-            }
-            if constexpr (ey != 0) {
-                const float2 A2 = n[2];
-                addrow(ey, A2.x, A2.y, A3.y);  // row y: (xy, yy, yz)
-            }
-            if constexpr (ez != 0) addrow(ez, A3.x, A3.y, A4.y);  // row z: (xz, yz, zz)
-            F[0] += vx;
-            F[1] += vy;
-            F[2] += vz;
-            G[0] = fmaf(ux, vx, G[0]);
-            G[1] = fmaf(uy, vy, G[1]);
-            G[2] = fmaf(uz, vz, G[2]);
-            G[3] = fmaf(uy, vx, fmaf(ux, vy, G[3]));
-            G[4] = fmaf(uz, vx, fmaf(ux, vz, G[4]));
-            G[5] = fmaf(uz, vy, fmaf(uy, vz, G[5]));
-        } else {
-            const float ux = A0.x, uy = A0.y;
-            float vx = 0.0f, vy = 0.0f;
-            if constexpr (ex != 0) {
-                const float2 A1 = n[1];
-                vx = ex * A1.x;
-                vy = ex * A1.y;
-            }
-            if constexpr (ey != 0) {
-                const float2 A2 = n[2];
-                if constexpr (ex != 0) {
-                    vx += ey * A2.x;
-                    vy += ey * A2.y;
-                } else {
-                    vx = ey * A2.x;
-                    vy = ey * A2.y;
-                }
-            }
-            F[0] += vx;
-            F[1] += vy;
-            G[0] = fmaf(ux, vx, G[0]);
-            G[1] = fmaf(uy, vy, G[1]);
-            G[2] = fmaf(uy, vx, fmaf(ux, vy, G[2]));
-        }
+        put_aux<D>(ax, u0, rb);
     }
 
     template <int I>
@@ -465,7 +361,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         constexpr int m = (D == 3) ? L::e(I, 2) : L::e(I, 1);
         const float2* as = (m == 1) ? ap : ((m == -1) ? am : a0);
         constexpr int r = L::e(I, 0) + ((D == 3) ? RX * L::e(I, 1) : 0);
-        grad_term<I>(as + (rc + r) * NA2, F, G);
+        grad_term<D, I>(as + (rc + r) * NA2, F, G);
     }
 
     template <int... Is>

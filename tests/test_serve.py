@@ -86,8 +86,10 @@ def test_matches_single_simulation(req):
     srv.close()
     rho, u, T = W.request_fields(req)
     tau, T0, thermal, bc = W.request_params(req)
+    # the server runs 1D requests on the generic tile body (tile 0) and 2D
+    # requests on the strip kernel's body (tile 3), 16 rows per work item
     sim = lbm.Simulation(req["dim"], req["nx"], req["ny"], 1, tau=tau, T0=T0, bc=bc, dtype="f32",
-                         thermal=thermal, tile=0, chunk=16)
+                         thermal=thermal, tile=3 if req["dim"] == 2 else 0, chunk=16)
     sim.init(rho, u, T)
     sim.step(req["steps"])
     r, uu, TT = sim.moments()
