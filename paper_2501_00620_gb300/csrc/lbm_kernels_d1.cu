@@ -5,7 +5,9 @@ namespace lbm {
 
 namespace {
 constexpr int kD = 1;
-constexpr Variant kVariants[] = {{256, 1}, {128, 1}};
+// Short strips spread small lattices (and FP64, whose rate on this part is a
+// small fraction of FP32's) over more multiprocessors.
+constexpr Variant kVariants[] = {{256, 1}, {128, 1}, {64, 1}, {32, 1}};
 constexpr int kNV = sizeof(kVariants) / sizeof(kVariants[0]);
 
 template <typename FS, int TX, int TY>
@@ -30,6 +32,8 @@ cudaError_t launch_dtype(int v, const StepArgs& a, cudaStream_t st) {
     switch (v) {
         case 0: return launch_one<FS, 256, 1>(a, st);
         case 1: return launch_one<FS, 128, 1>(a, st);
+        case 2: return launch_one<FS, 64, 1>(a, st);
+        case 3: return launch_one<FS, 32, 1>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -39,6 +43,8 @@ size_t smem_of(int v) {
     switch (v) {
         case 0: return StepShape<kD, FS, 256, 1>::smem;
         case 1: return StepShape<kD, FS, 128, 1>::smem;
+        case 2: return StepShape<kD, FS, 64, 1>::smem;
+        case 3: return StepShape<kD, FS, 32, 1>::smem;
         default: return 0;
     }
 }
