@@ -95,7 +95,12 @@ typedef struct {
     void *alloc_ctx;
     int tile;               /* kernel variant index; -1 (default): autotuned */
     int chunk;              /* planes per block along the march axis; 0: auto */
-    int steps_per_launch;   /* small lattices: steps fused per launch; 0: auto */
+    int steps_per_launch;   /* 1D lattices: steps per cooperative launch (a
+                               grid-wide barrier between steps, the same bits
+                               as single steps); 0 (default): the faster of
+                               64 per launch and CUDA-graph replays of single
+                               steps, timed at the first lbm_step on scratch
+                               copies of the state; 1: single steps */
     int diagnostics;        /* 1 (default): every step also reduces mass,
                                momentum and energy of the state it consumes
                                into a device history (lbm_diagnostics_history);
@@ -186,8 +191,10 @@ lbm_status lbm_flags(lbm_sim *sim, int *flags);
 long lbm_step_count(const lbm_sim *sim);
 
 /* The launch configuration of the step (library service, no counterpart in
- * the paper): *tile = the tile variant in use (0.. the generic fused kernel,
- * 100.. the shared-memory-staged kernels), *chunk = planes per thread block
+ * the paper): *tile = the tile variant in use (0.. the generic fused kernel;
+ * on D2Q9 3 = the strip kernel; 100.. the shared-memory-staged kernels;
+ * *kernel = "step_multi_kernel" when 1D steps run several per cooperative
+ * launch), *chunk = planes per thread block
  * along the slowest axis, *kernel = name of the kernel template (static
  * string).  Fixed by opts.tile/opts.chunk or by the autotuner at the first
  * lbm_step; before that *tile = *chunk = -1 and *kernel = "".  Any pointer

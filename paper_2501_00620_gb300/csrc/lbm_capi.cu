@@ -83,6 +83,7 @@ struct lbm_sim {
     double* diag_out = nullptr;
     double* fields = nullptr;  // (D+2) N doubles: init input / moments output
     int var = -1, chunk = 0;
+    int multi_k = 0;  // D1: steps per cooperative launch (0: not decided, 1: single steps)
     long nstep = 0;
     // graphs: [parity of cur] -> executable graph of kGraphSteps launches
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -286,6 +287,120 @@ lbm_status launch_one_step(lbm_sim* s, bool diag) {
     lbm_status st = launch_variant(s, s->var, a, s->cur);
     if (st != LBM_OK) return st;
     s->cur = 1 - s->cur;
+    return LBM_OK;
+}
+
+// K steps of a D1 lattice in one cooperative launch from the current buffer.
+lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* const* b) {
+    StepArgs a[2];
+    for (int p = 0; p < 2; ++p) {
+        a[p] = base_args(s);
+        a[p].fin = f[p];
+        a[p].bin = b[p];
+        a[p].fout = f[1 - p];
+        a[p].bout = b[1 - p];
+        a[p].write_state = 1;
+        a[p].want_diag = diag ? 1 : 0;
+        a[p].hist = s->hist;
+    }
+    const int c = s->cur;
+    cudaError_t e = launch_step_multi_d1(s->dtype, s->var, a[c], a[1 - c], K, s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, std::string("multi-step launch: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+// D1: steps per launch.  opts.steps_per_launch > 1 forces a length; 0 times a
+// replay of 64 single-step launches (CUDA graph) against one 64-step
+// cooperative launch on scratch copies of the state, and keeps the faster.
+lbm_status tune_multi(lbm_sim* s) {
+    s->multi_k = 1;
+    if (s->D != 1 || s->opts.steps_per_launch == 1) return LBM_OK;
+    if (s->opts.steps_per_launch > 1) {  // forced
+        s->multi_k = s->opts.steps_per_launch;
+        return LBM_OK;
+    }
+    const int K = 64;
+    // scratch copies of the state, from the caller's allocator if one is set
+    auto tmp_alloc = [s](size_t n) -> void* {
+        void* p = nullptr;
+        if (s->opts.alloc) return s->opts.alloc(n, s->opts.alloc_ctx);
+        return cudaMalloc(&p, n) == cudaSuccess ? p : nullptr;
+    };
+    auto tmp_free = [s](void* p, size_t n) {
+        if (!p) return;
+        if (s->opts.alloc)
+            s->opts.free(p, n, s->opts.alloc_ctx);
+        else
+            cudaFree(p);
+    };
+    const size_t fb = (size_t)s->Q * s->N * fbytes_of(s->dtype), bb = (size_t)s->NB * s->N * rbytes_of(s->dtype);
+    void *tf[2] = {nullptr, nullptr}, *tb[2] = {nullptr, nullptr};
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        tf[k] = tmp_alloc(fb);
+        tb[k] = tmp_alloc(bb);
+        ok = tf[k] && tb[k];
+    }
+    float t_multi = 1e30f, t_graph = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // the scratch runs may raise the flag word on a bad state: keep its value
+    int flag0 = 0;
+    if (cudaMemcpy(&flag0, s->flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+    if (ok) ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (ok) {
+        for (int k = 0; k < 2; ++k) {
+            cudaMemcpyAsync(tf[k], s->f[s->cur], fb, cudaMemcpyDeviceToDevice, s->stream);
+            cudaMemcpyAsync(tb[k], s->b[s->cur], bb, cudaMemcpyDeviceToDevice, s->stream);
+        }
+        // the timing runs write a scratch flag word only if the state is bad;
+        // diagnostics off, the history untouched
+        if (launch_multi(s, K, false, tf, tb) == LBM_OK) {
+            cudaEventRecord(e0, s->stream);
+            launch_multi(s, K, false, tf, tb);
+            cudaEventRecord(e1, s->stream);
+            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t_multi, e0, e1);
+        }
+        cudaGetLastError();
+        {
+            // single steps on the same scratch buffers, captured as one graph
+            void* sf[2] = {s->f[0], s->f[1]};
+            void* sb[2] = {s->b[0], s->b[1]};
+            s->f[0] = tf[0], s->f[1] = tf[1], s->b[0] = tb[0], s->b[1] = tb[1];
+            cudaGraphExec_t ge = nullptr;
+            cudaGraph_t g;
+            if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                lbm_status st = LBM_OK;
+                for (int k = 0; k < K && st == LBM_OK; ++k) st = launch_one_step(s, false);
+                if (cudaStreamEndCapture(s->stream, &g) == cudaSuccess) {
+                    if (st == LBM_OK && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+                        cudaGraphLaunch(ge, s->stream);
+                        cudaEventRecord(e0, s->stream);
+                        cudaGraphLaunch(ge, s->stream);
+                        cudaEventRecord(e1, s->stream);
+                        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t_graph, e0, e1);
+                        cudaGraphExecDestroy(ge);
+                    }
+                    cudaGraphDestroy(g);
+                }
+            }
+            cudaGetLastError();
+            s->f[0] = sf[0], s->f[1] = sf[1], s->b[0] = sb[0], s->b[1] = sb[1];
+            // launch_one_step flipped s->cur K times: K is even
+        }
+    }
+    cudaStreamSynchronize(s->stream);
+    if (ok) cudaMemcpy(s->flag, &flag0, sizeof(int), cudaMemcpyHostToDevice);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int k = 0; k < 2; ++k) {
+        tmp_free(tf[k], fb);
+        tmp_free(tb[k], bb);
+    }
+    cudaGetLastError();
+    if (t_multi < t_graph) s->multi_k = K;
     return LBM_OK;
 }
 
@@ -571,6 +686,24 @@ lbm_status lbm_step(lbm_sim* s, long n) {
     const bool diag = s->opts.diagnostics != 0;
     const int K = s->graph_steps;
     long done = 0;
+    if (s->multi_k == 0) {
+        st = tune_multi(s);
+        if (st != LBM_OK) return st;
+    }
+    if (s->multi_k > 1) {
+        // D1: several steps per cooperative launch
+        void* f[2] = {s->f[0], s->f[1]};
+        void* b[2] = {s->b[0], s->b[1]};
+        while (done < n) {
+            const int k = (int)std::min<long>(s->multi_k, n - done);
+            st = launch_multi(s, k, diag, f, b);
+            if (st != LBM_OK) return st;
+            if (k & 1) s->cur = 1 - s->cur;
+            done += k;
+        }
+        s->nstep += n;
+        return LBM_OK;
+    }
     if (s->opts.use_graphs && s->stream != nullptr && n >= 2) {
         if (K == 0) {
             // graph length: more launches per replay for small lattices
@@ -609,7 +742,8 @@ lbm_status lbm_launch_config(const lbm_sim* s, int* tile, int* chunk, const char
     if (!s) return fail(LBM_EINVAL, "NULL simulation");
     if (tile) *tile = s->var;
     if (chunk) *chunk = s->var >= 0 ? s->chunk : -1;
-    if (kernel) *kernel = s->var >= 0 ? kernel_name(s->D, s->var) : "";
+    if (kernel)
+        *kernel = s->var < 0 ? "" : (s->multi_k > 1 ? "step_multi_kernel" : kernel_name(s->D, s->var));
     return LBM_OK;
 }
 

@@ -43,6 +43,11 @@ cudaError_t tma_box(int D, int dtype, int v, TmaBox* box);
 dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk);
 
 cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t st);
+// K steps of the D1 lattice in one cooperative launch (generic variant v):
+// a0 reads buffer 0, a1 buffer 1; step k uses a0 if k is even.  Returns
+// cudaErrorCooperativeLaunchTooLarge if the grid cannot be resident.
+cudaError_t launch_step_multi_d1(int dtype, int v, const StepArgs& a0, const StepArgs& a1, int K,
+                                 cudaStream_t st);
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st);
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
                         void* b, long long N, cudaStream_t st);

@@ -27,6 +27,39 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// K steps per cooperative launch; cudaErrorCooperativeLaunchTooLarge if the
+// grid cannot be resident at once (the caller then launches single steps).
+template <typename FS, int TX>
+cudaError_t launch_multi_one(const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st) {
+    using Sh = StepShape<kD, FS, TX, 1>;
+    auto kern = step_multi_kernel<kD, FS, TX, 1>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int blocks = (a0.nx + TX - 1) / TX;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX, Sh::smem);
+    if (e != cudaSuccess) return e;
+    if ((long long)per_sm * device_sms() < blocks) return cudaErrorCooperativeLaunchTooLarge;
+    StepArgs p0 = a0, p1 = a1;
+    void* args[] = {&p0, &p1, &K};
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(TX), args, Sh::smem, st);
+}
+
+template <typename FS>
+cudaError_t launch_multi_dtype(int v, const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st) {
+    switch (v) {
+        case 0: return launch_multi_one<FS, 256>(a0, a1, K, st);
+        case 1: return launch_multi_one<FS, 128>(a0, a1, K, st);
+        case 2: return launch_multi_one<FS, 64>(a0, a1, K, st);
+        case 3: return launch_multi_one<FS, 32>(a0, a1, K, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename FS>
 cudaError_t launch_dtype(int v, const StepArgs& a, cudaStream_t st) {
     switch (v) {
@@ -65,6 +98,11 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 
 cudaError_t launch_step_d1(int dtype, int v, const StepArgs& a, cudaStream_t st) {
     return by_dtype(dtype, [&](auto tag) { return launch_dtype<decltype(tag)>(v, a, st); });
+}
+
+cudaError_t launch_step_multi_d1(int dtype, int v, const StepArgs& a0, const StepArgs& a1, int K,
+                                 cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) { return launch_multi_dtype<decltype(tag)>(v, a0, a1, K, st); });
 }
 
 size_t step_smem_d1(int dtype, int v) {

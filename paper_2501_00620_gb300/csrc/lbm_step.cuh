@@ -18,6 +18,7 @@
 // once per step.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cstdint>
 
 #include "lbm_site.cuh"
@@ -251,6 +252,22 @@ template <int D, typename FS, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) step_kernel(const StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_block<D, FS, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// K steps in one cooperative launch (small lattices, where a launch costs
+// more than the step): the blocks run the tile body on the arguments of the
+// current parity (a[0] reads buffer 0, a[1] buffer 1) and meet at a
+// grid-wide barrier after every step.  Every block must be resident; the
+// launcher checks that before it launches.
+template <int D, typename FS, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) step_multi_kernel(const StepArgs a0, const StepArgs a1, int K) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    for (int k = 0; k < K; ++k) {
+        step_block<D, FS, TX, TY>((k & 1) ? a1 : a0, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+        __syncthreads();  // the next step reuses shared memory
+        grid.sync();
+    }
 }
 
 // ---------------------------------------------------------------------------

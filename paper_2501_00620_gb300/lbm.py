@@ -299,7 +299,7 @@ class Simulation:
 
     def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
                  thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
-                 use_graphs=True, torch_allocator=False):
+                 use_graphs=True, torch_allocator=False, steps_per_launch=0):
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -313,6 +313,7 @@ class Simulation:
         o.chunk = chunk
         o.diagnostics = int(bool(diagnostics))
         o.use_graphs = int(bool(use_graphs))
+        o.steps_per_launch = int(steps_per_launch)
         self._allocator = None
         if torch_allocator:
             self._allocator = TorchAllocator(device)
