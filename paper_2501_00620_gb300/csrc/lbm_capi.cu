@@ -174,8 +174,8 @@ bool tma_applicable(const lbm_sim* s, int v) {
     if (s->nx < 2 || (s->D == 3 && s->ny < 2)) return false;
     // the march index wraps with one conditional add or subtract
     if ((s->D == 3 ? s->nz : s->ny) < 4) return false;
-    // site indices are 32-bit in the staged kernels
-    if (s->N >= (1LL << 31)) return false;
+    // plane offsets i N + s and variance offsets are 32-bit in the staged kernels
+    if ((long long)s->Q * s->N >= (1LL << 31)) return false;
     return encode_fn() != nullptr;
 }
 

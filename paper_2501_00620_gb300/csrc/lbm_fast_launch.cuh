@@ -16,9 +16,10 @@ struct FastVariant {
     int tx, ty, pfb, mb, persist;
 };
 
-// D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 8 persistent;
-// 32 x 4 with one more variance plane in flight.
-constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 8, 0, 2, 1}, {32, 4, 1, 3, 0}};
+// D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 4 with one more
+// variance plane in flight at two (room for ~146 registers a thread) and at
+// three blocks per SM.
+constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 1, 2, 0}, {32, 4, 1, 3, 0}};
 // D2Q9: strips of 128 or 64 sites; 128 persistent.
 constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {64, 1, 0, 8, 0}, {128, 1, 0, 5, 1}};
 

@@ -48,7 +48,7 @@ cudaError_t launch_strip(const StepArgs& a, cudaStream_t st) {
     if constexpr (std::is_same<FS, double>::value) {
         return cudaErrorInvalidValue;  // FP32 arithmetic only
     } else {
-        if (a.N >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit site indices
+        if (9 * a.N >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit plane offsets i N + s
         return a.fixed_x ? launch_strip_fx<FS, true>(a, st) : launch_strip_fx<FS, false>(a, st);
     }
 }

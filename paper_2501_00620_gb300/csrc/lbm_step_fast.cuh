@@ -64,6 +64,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr uint32_t BBYTES = NB * BSLICE * 4;             // transaction bytes per variance slot
     static_assert((D == 3 ? 2 * SXB : SXB) <= 256 && SY <= 256, "TMA box edges are limited to 256 elements");
     static_assert(NT <= 1024, "too many threads");
+    static_assert(4 * SY + ((D == 3) ? 4 * (TX + 4) : 0) <= NT, "one halo item per thread at most");
     static_assert(MB * (SMEM + 1024) <= 228 * 1024, "MB blocks do not fit in shared memory");
 };
 
@@ -210,6 +211,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     // transport reads x in {-2,-1} / {nx,nx+1} (all slice rows) and, in 3D,
     // y in {-2,-1} / {ny,ny+1} (x from x0-2 to x0+TX+1): those positions get
     // the periodic image or the fixed-state reservoir.
+    // halo items of this block per plane: at most 4 SY + 4 (TX + 4) <= NT
     __device__ __forceinline__ int halo_count() const {
         const int cx = (xlo ? 2 : 0) + (xhi ? 2 : 0);
         const int cy = (ylo ? 2 : 0) + (yhi ? 2 : 0);
@@ -228,36 +230,45 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             gy = (ylo && rr < 2) ? -2 + rr : ny + (rr - (ylo ? 2 : 0));
         }
     }
+    // This thread's halo item (at most one: halo_count() <= NT), fixed for
+    // the segment: its slot position and source column/row, computed once.
+    int h_off = -1;   // float offset (2D) or float2 offset (3D) in a slot; -1: no item
+    int h_src = 0;    // in-plane source index wx + nx wy (3D) or wx (2D)
+    int h_wy = 0;     // source row y (3D)
+    int h_res = -1;   // fixed-state reservoir side (0, 1) or -1
+    __device__ __forceinline__ void setup_halo() {
+        if (!edge || tid >= halo_count()) return;
+        int gx, gy;
+        halo_pos(tid, gx, gy);
+        const int sx = gx - (x0 - PXB), sy = (D == 3) ? gy - (y0 - 2) : 0;
+        h_off = sy * SXB + sx;
+        h_wy = (D == 3) ? wrap(gy, ny) : 0;
+        h_src = wrap(gx, nx) + ((D == 3) ? nx * h_wy : 0);
+        if (FX && (gx < 0 || gx >= nx)) h_res = gx < 0 ? 0 : 1;
+    }
     __device__ __forceinline__ void patch_b(int q) {
-        const float* __restrict__ bin = static_cast<const float*>(a.bin);
-        const float* __restrict__ gb = static_cast<const float*>(a.gb);
-        float* slot = bslot(bs_of(q));
-        const int plane = wrapq(q);
-        const int cnt = halo_count();
-        for (int k = tid; k < cnt; k += Sh::NT) {
-            int gx, gy;
-            halo_pos(k, gx, gy);
-            const int sx = gx - (x0 - PXB), sy = (D == 3) ? gy - (y0 - 2) : 0;
-            const int wy = (D == 3) ? wrap(gy, ny) : plane;
-            const int wx = wrap(gx, nx);
-            const int row = (D == 3) ? wy + ny * plane : plane;
-            const int s = wx + nx * row;
-            const bool res = FX && (gx < 0 || gx >= nx);
+        if (h_off >= 0) {
+            const float* __restrict__ bin = static_cast<const float*>(a.bin);
+            const float* __restrict__ gb = static_cast<const float*>(a.gb);
+            float* slot = bslot(bs_of(q));
+            const int plane = wrapq(q);
+            const int s = h_src + pstride * plane;
+            const int row = (D == 3) ? h_wy + ny * plane : plane;
             float v[NB];
 #pragma unroll
             for (int k2 = 0; k2 < NB; ++k2)
-                v[k2] = res ? gb[((gx < 0 ? 0 : 1) * NB + k2) * (int)a.rows + row]
-                            : bin[BLayout<D, FS>::at(k2, s, Ni)];
+                v[k2] = (FX && h_res >= 0) ? gb[(h_res * NB + k2) * (int)a.rows + row]
+                                           : bin[(int)BLayout<D, FS>::at(k2, s, Ni)];
             if (D == 3) {
-                float2* s2 = reinterpret_cast<float2*>(slot) + sy * SXB + sx;
+                float2* s2 = reinterpret_cast<float2*>(slot) + h_off;
 #pragma unroll
                 for (int p = 0; p < NB / 2; ++p) s2[p * BSLICE] = make_float2(v[2 * p], v[2 * p + 1]);
             } else {
 #pragma unroll
-                for (int k2 = 0; k2 < NB; ++k2) slot[k2 * BSLICE + sx] = v[k2];
+                for (int k2 = 0; k2 < NB; ++k2) slot[k2 * BSLICE + h_off] = v[k2];
             }
+            fence_proxy_async_smem();  // the slot is refilled by a bulk copy later
         }
-        fence_proxy_async_smem();  // the slot is refilled by a bulk copy later
     }
 
     // ---- stage 1: pull + moments of this thread's region site at plane q -------
@@ -454,6 +465,7 @@ __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* s
         }
     }
     blk.set_site(rx, ry);
+    blk.setup_halo();
 
     // prologue: variance planes p0-2 .. p0+PFB (the slots' first fill)
     if (tid == 0) fence_proxy_async_smem();  // slots may hold generic-proxy halo writes of a previous segment
