@@ -9,7 +9,8 @@
 
 namespace lbm {
 
-// Tile TX x TY, extra variance prefetch planes PFB, resident blocks per SM MB,
+// Tile TX x TY, PFB flags (bit 0: extra variance plane in flight, bit 1:
+// populations to stage 2 through shared memory), resident blocks per SM MB,
 // persistent grid (balanced shares of the column x plane work) or one block
 // per (tile, chunk).
 struct FastVariant {
@@ -17,9 +18,10 @@ struct FastVariant {
 };
 
 // D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 4 with one more
-// variance plane in flight at two (room for ~146 registers a thread) and at
-// three blocks per SM.
-constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 1, 2, 0}, {32, 4, 1, 3, 0}};
+// variance plane in flight and the populations handed to stage 2 through
+// shared memory, at two blocks per SM; 32 x 4 with one more variance plane
+// in flight at three.
+constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 3, 2, 0}, {32, 4, 1, 3, 0}};
 // D2Q9: strips of 128 or 64 sites; 128 persistent.
 constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {64, 1, 0, 8, 0}, {128, 1, 0, 5, 1}};
 

@@ -10,8 +10,8 @@
 //   shared memory would buy no reuse.
 // * The variance planes, which the mass-weighted transport (Eq. 66) reads at
 //   all Q neighbours, are staged by tiled bulk tensor copies (TMA) in a ring
-//   of 3 + PFB plane slots.  In 3D they are stored as component pairs, so the
-//   transport reads one 8-byte pair per neighbour and accumulates it with the
+//   of 3 + PF plane slots (PF = PFB & 1).  In 3D they are stored as component
+//   pairs, so the transport reads one 8-byte pair per neighbour and accumulates it with the
 //   packed FP32x2 multiply-add of sm_100+ (two FP32 FMAs per instruction).
 // * (u0, rho b) of the tile plus a one-site ring live in four shared plane
 //   slots, site-major as float2 pairs grouped by the rows of rho b that a
@@ -39,8 +39,13 @@
 
 namespace lbm {
 
+// PFB: bit 0 -- one more variance plane in flight; bit 1 -- a tile site hands
+// its pulled populations to stage 2 through shared memory instead of pulling
+// them a second time.  MB: resident blocks per SM the launch bounds aim at.
 template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape {
     using L = Lattice<D>;
+    static constexpr int PF = PFB & 1;
+    static constexpr bool DFS = (PFB & 2) != 0;
     static constexpr int Q = L::Q, NB = L::NB;
     static constexpr int PXB = 4;                                   // 16-byte aligned x start of a b copy
     static constexpr int SXB = TX + 2 * PXB;                        // sites per staged row
@@ -54,11 +59,12 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr int NT = round_up(NINT + NRING, 32);
     static constexpr int BSLICE = SY * SXB;                         // sites of one staged slice
     static constexpr int BPITCH = round_up(NB * BSLICE * 4, 128);   // bytes between variance slots
-    static constexpr int NBS = 3 + PFB, NAS = 4;
+    static constexpr int NBS = 3 + PF, NAS = 4;
     static constexpr int NSV = NB + D + 2;                          // carried site values: bbar, rho, j0, Ebar
     static constexpr int OFF_AUX = NBS * BPITCH;
     static constexpr int OFF_SV = OFF_AUX + round_up(NAS * NA2 * 8 * RS, 16);
-    static constexpr int OFF_RED = OFF_SV + 2 * NSV * NINT * 4;
+    static constexpr int OFF_DF = OFF_SV + 2 * NSV * NINT * 4;      // DFS: [2][Q][NINT] populations
+    static constexpr int OFF_RED = OFF_DF + (DFS ? 2 * Q * NINT * 4 : 0);
     static constexpr int OFF_BAR = OFF_RED + 32 * (D + 2) * 8;
     static constexpr int SMEM = OFF_BAR + NBS * 8;
     static constexpr uint32_t BBYTES = NB * BSLICE * 4;             // transaction bytes per variance slot
@@ -111,7 +117,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     }
 
     static __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-    // q ranges over [p0 - 3, p1 + 2 + PFB] with PFB + 3 <= np: one conditional add or subtract wraps it
+    // q ranges over [p0 - 3, p1 + 2 + PF] with PF + 3 <= np: one conditional add or subtract wraps it
     __device__ __forceinline__ int wrapq(int q) const { return wrap(q, np); }
     static __device__ __forceinline__ int march(int i) { return (D == 3) ? L::e(i, 2) : L::e(i, 1); }
 
@@ -127,6 +133,10 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         return reinterpret_cast<float*>(smem + Sh::OFF_SV) + (q & 1) * Sh::NSV * Sh::NINT + tid;
     }
     __device__ __forceinline__ int bs_of(int q) const { return (q - (p0 - 2)) % Sh::NBS; }
+    // DFS: populations of plane q for tile site t: population i at [i * NINT + t]
+    __device__ __forceinline__ float* dfs(int q) const {
+        return reinterpret_cast<float*>(smem + Sh::OFF_DF) + (q & 1) * Q * Sh::NINT + tid;
+    }
 
     // Region site (rx, ry) of this thread: x from x0 - 1, y from y0 - 1.
     __device__ __forceinline__ void set_site(int rx_, int ry_) {
@@ -354,6 +364,11 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         step_params(a, omega, tau, T0);
         site_moments<D, float>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
         if (tile) {
+            if constexpr (Sh::DFS) {
+                float* dv = dfs(q);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) dv[i * Sh::NINT] = df[i];
+            }
             float* v = sv(q);
             constexpr int NI = Sh::NINT;
 #pragma unroll
@@ -424,7 +439,13 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         for (int c = 0; c < D; ++c) c_j[c] = v[(NB + 1 + c) * NI];
         const float c_E = v[(NB + 1 + D) * NI];
         float df[Q];
-        pull(p, zsp, df);  // second pull of the same values
+        if constexpr (Sh::DFS) {
+            const float* dv = dfs(p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) df[i] = dv[i * Sh::NINT];
+        } else {
+            pull(p, zsp, df);  // second pull of the same values
+        }
         site_collide<D, FS, float, int, DiagDev<D + 2>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     }
 };
@@ -467,9 +488,9 @@ __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* s
     blk.set_site(rx, ry);
     blk.setup_halo();
 
-    // prologue: variance planes p0-2 .. p0+PFB (the slots' first fill)
+    // prologue: variance planes p0-2 .. p0+PF (the slots' first fill)
     if (tid == 0) fence_proxy_async_smem();  // slots may hold generic-proxy halo writes of a previous segment
-    for (int q = p0 - 2; q <= min(p0 + PFB, p1 + 1); ++q) {
+    for (int q = p0 - 2; q <= min(p0 + Sh::PF, p1 + 1); ++q) {
         if (tid == 0) blk.issue_b(q);
         blk.b_pending |= 1u << blk.bs_of(q);
     }
@@ -502,7 +523,7 @@ __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* s
             }
             return false;
         }
-        const int qn = q + 2 + PFB;
+        const int qn = q + 2 + Sh::PF;
         if (qn <= p1 + 1) {
             if (tid == 0) {
                 fence_proxy_async_smem();
