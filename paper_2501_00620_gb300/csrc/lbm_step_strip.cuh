@@ -226,7 +226,20 @@ __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, u
         }
     }
     __syncthreads();
+    // L2 prefetch of this site's populations in row P (all Q planes): the
+    // first pull from row P is made by stage 1 of row P - 1
+    auto prefetch_row = [&](int P) {
+        if (!active || reservoir) return;
+        const int s = gxw + nx * wrapq(P);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const FS* pp = fin + i * Ni + s;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
+        }
+    };
+    for (int r = p0 - 2; r <= min(p0 + 1, p1 + 1); ++r) prefetch_row(r);
     for (int q = p0 - 1; q <= p1; ++q) {
+        if (q + 3 <= p1 + 1) prefetch_row(q + 3);
         // variance row q+2 (read by stage 1 of row q+1) into registers now,
         // into its slot -- that of row q-2, last read before the previous
         // barrier -- after stage 1
