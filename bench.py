@@ -44,7 +44,7 @@ WORKLOAD_TEXT = {
 }
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=1000)
@@ -60,7 +60,26 @@ def parse():
     p.add_argument("--chunk", type=int, default=0, help="force planes per block (0: autotuned)")
     p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
     p.add_argument("--no-sequential", action="store_true", help="serve: skip the one-at-a-time comparison")
-    return p.parse_args()
+    return p.parse_args(argv)
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """Largest value of x over all ranks -- the slowest rank's time decides a
+    step of the whole job.  One all-reduce of a one-element tensor on
+    `device` (cuda under NCCL, cpu under gloo); x itself without a process
+    group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units all ranks processed per second when every rank does the same
+    work (weak scaling) and the slowest rank's time counts."""
+    return world * units_per_rank / seconds_max
 
 
 def dist_env():
@@ -359,14 +378,10 @@ def run_serve(args):
     st = srv.stats()
     clocks = sampler.stop()
     srv.close()
-    wall = st["last_done_s"] - max(st["first_submit_s"], base["last_done_s"])
-    tt = torch.tensor([wall], device="cuda")
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    wall = float(tt.item())
+    wall = max_over_ranks(st["last_done_s"] - max(st["first_submit_s"], base["last_done_s"]), dist)
     busy = st["busy_s"] - base["busy_s"]
     rounds = st["rounds"] - base["rounds"]
-    value = world * updates / wall / 1e6
+    value = whole_job_rate(updates, world, wall) / 1e6
 
     seq = None
     if not args.no_sequential:
@@ -489,11 +504,8 @@ def main():
     clocks = sampler.stop()
     sim.sync()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(N * args.steps, world, ms_max * 1e-3) / 1e6
     ms_per_step = ms_max / args.steps
 
     # roofline of the step kernel (one launch per step)
@@ -519,14 +531,10 @@ def main():
             lbm.lbm_step(sim.h, 1)
             lbm.lbm_last_diagnostics(sim.h, rec)
         lbm.lbm_moments(sim.h, orr, ou, oT)
-        te = time.perf_counter() - t0
-        tt = torch.tensor([te], device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - t0, dist)
         h2d = (2 + d) * N * 8
         d2h = (d + 3) * 8 * args.steps + (2 + d) * N * 8
-        e2e = {"value": world * N * args.steps / te / 1e6, "unit": "MLUPS",
+        e2e = {"value": whole_job_rate(N * args.steps, world, te) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "lbm_init from pinned host fields, per step lbm_step(1) + lbm_last_diagnostics "
                            "(d+3 doubles D2H), final lbm_moments (rho, u, T D2H)"}
