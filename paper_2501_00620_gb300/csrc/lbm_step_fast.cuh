@@ -381,26 +381,6 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         put_aux<D>(ax, u0, rb);
     }
 
-    template <int I>
-    __device__ __forceinline__ void grad_at(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
-                                            float* G) const {
-        constexpr int m = (D == 3) ? L::e(I, 2) : L::e(I, 1);
-        const float2* as = (m == 1) ? ap : ((m == -1) ? am : a0);
-        constexpr int r = L::e(I, 0) + ((D == 3) ? RX * L::e(I, 1) : 0);
-        grad_term<D, I>(as + (rc + r) * NA2, F, G);
-    }
-
-    template <int... Is>
-    __device__ __forceinline__ void grad_axes(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
-                                              float* G, std::integer_sequence<int, Is...>) const {
-        ((norm2<D>(Is + 1) == 1 ? grad_at<Is + 1>(am, a0, ap, rc, F, G) : void()), ...);
-    }
-    template <int... Is>
-    __device__ __forceinline__ void grad_edges(const float2* am, const float2* a0, const float2* ap, int rc, float* F,
-                                               float* G, std::integer_sequence<int, Is...>) const {
-        ((norm2<D>(Is + 1) == 2 ? grad_at<Is + 1>(am, a0, ap, rc, F, G) : void()), ...);
-    }
-
     // ---- stage 2: gradients, collision and store of this tile site at plane p ----
     __device__ __forceinline__ void stage2(int p, const int* zsp, DiagDev<D + 2>& acc, int& bad) {
         const int s = xs[1] + ((D == 3) ? ys[1] : 0) + zsp[1];
@@ -409,26 +389,14 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         const float2* a0 = aux(p);
         const float2* ap = aux(p + 1);
         float F[D], G[NB];
-#pragma unroll
-        for (int c = 0; c < D; ++c) F[c] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] = 0.0f;
-        // F = -3 sum_i w_i v_i, G = -3 sum_i w_i (u v + v u): the axis terms
-        // carry w_axis = (w_axis / w_edge) w_edge, so sum them first, scale by
-        // that ratio (2 on D3Q19, 4 on D2Q9), then add the edge terms and
-        // scale everything by -3 w_edge (diagonal of G: twice that).
-        grad_axes(am, a0, ap, rc, F, G, std::make_integer_sequence<int, Q - 1>{});
-        constexpr float ratio = float(L::w(1) / L::w(Q - 1));
-#pragma unroll
-        for (int c = 0; c < D; ++c) F[c] *= ratio;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] *= ratio;
-        grad_edges(am, a0, ap, rc, F, G, std::make_integer_sequence<int, Q - 1>{});
-        constexpr float sc = float(-3.0 * L::w(Q - 1));
-#pragma unroll
-        for (int c = 0; c < D; ++c) F[c] *= sc;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) G[k] *= (k < D ? 2.0f * sc : sc);
+        gradients<D>(
+            [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int m = (D == 3) ? L::e(i, 2) : L::e(i, 1);
+                const float2* as = (m == 1) ? ap : ((m == -1) ? am : a0);
+                return as + (rc + L::e(i, 0) + ((D == 3) ? RX * L::e(i, 1) : 0)) * NA2;
+            },
+            F, G);
         const float* v = sv(p);
         constexpr int NI = Sh::NINT;
         float c_bt[NB], c_j[D];
