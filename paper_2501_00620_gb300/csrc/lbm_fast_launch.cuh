@@ -22,8 +22,9 @@ struct FastVariant {
 // shared memory, at two blocks per SM; 32 x 4 with one more variance plane
 // in flight at three.
 constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 3, 2, 0}, {32, 4, 1, 3, 0}};
-// D2Q9: strips of 128 or 64 sites; 128 persistent.
-constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {64, 1, 0, 8, 0}, {128, 1, 0, 5, 1}};
+// D2Q9: strips of 128 or 64 sites; 128 with the populations handed to
+// stage 2 through shared memory; 128 persistent.
+constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {128, 1, 3, 5, 0}, {128, 1, 0, 5, 1}};
 
 
 template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX, bool PERSIST>
