@@ -258,7 +258,7 @@ std::vector<int> chunk_candidates(const lbm_sim* s) {
     int np = s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1);
     if (s->D == 1) return {1};
     std::vector<int> c;
-    for (int k : {8, 12, 16, 24, 32, 64, 128, 256}) {
+    for (int k : {8, 10, 12, 14, 16, 20, 24, 28, 32, 64, 128, 256}) {
         if (k >= np) {
             c.push_back(np);
             break;
