@@ -20,8 +20,9 @@ struct FastVariant {
 // D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 4 with one more
 // variance plane in flight and the populations handed to stage 2 through
 // shared memory, at two blocks per SM; 32 x 4 with one more variance plane
-// in flight at three.
-constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 3, 2, 0}, {32, 4, 1, 3, 0}};
+// in flight at three; the third with the hand-off in tensor memory at three.
+constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 3, 2, 0}, {32, 4, 1, 3, 0},
+                                  {32, 4, 7, 3, 0}};
 // D2Q9: strips of 128 or 64 sites; 128 with the populations handed to
 // stage 2 through shared memory; 128 persistent.
 constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {128, 1, 3, 5, 0}, {128, 1, 0, 5, 1}};
@@ -76,6 +77,7 @@ cudaError_t fast_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t 
             LBM_FAST_CASE(3, kFast3, 1)
             LBM_FAST_CASE(3, kFast3, 2)
             LBM_FAST_CASE(3, kFast3, 3)
+            LBM_FAST_CASE(3, kFast3, 4)
             default: return cudaErrorInvalidValue;
         }
     } else {

@@ -41,11 +41,14 @@ namespace lbm {
 
 // PFB: bit 0 -- one more variance plane in flight; bit 1 -- a tile site hands
 // its pulled populations to stage 2 through shared memory instead of pulling
-// them a second time.  MB: resident blocks per SM the launch bounds aim at.
+// them a second time; bit 2 (with bit 1) -- those populations and the site
+// values live in tensor memory (TMEM) instead of shared memory, so that more
+// blocks fit per SM.  MB: resident blocks per SM the launch bounds aim at.
 template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape {
     using L = Lattice<D>;
     static constexpr int PF = PFB & 1;
     static constexpr bool DFS = (PFB & 2) != 0;
+    static constexpr bool TM = (PFB & 4) != 0;
     static constexpr int Q = L::Q, NB = L::NB;
     static constexpr int PXB = 4;                                   // 16-byte aligned x start of a b copy
     static constexpr int SXB = TX + 2 * PXB;                        // sites per staged row
@@ -63,10 +66,17 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr int NSV = NB + D + 2;                          // carried site values: bbar, rho, j0, Ebar
     static constexpr int OFF_AUX = NBS * BPITCH;
     static constexpr int OFF_SV = OFF_AUX + round_up(NAS * NA2 * 8 * RS, 16);
-    static constexpr int OFF_DF = OFF_SV + 2 * NSV * NINT * 4;      // DFS: [2][Q][NINT] populations
-    static constexpr int OFF_RED = OFF_DF + (DFS ? 2 * Q * NINT * 4 : 0);
+    static constexpr int OFF_DF = OFF_SV + (TM ? 0 : 2 * NSV * NINT * 4);  // DFS: [2][Q][NINT] populations
+    static constexpr int OFF_RED = OFF_DF + (DFS && !TM ? 2 * Q * NINT * 4 : 0);
     static constexpr int OFF_BAR = OFF_RED + 32 * (D + 2) * 8;
-    static constexpr int SMEM = OFF_BAR + NBS * 8;
+    static constexpr int OFF_TADDR = OFF_BAR + NBS * 8;               // TM: TMEM base address
+    static constexpr int SMEM = OFF_TADDR + 16;
+    // TM: per tile thread 2 planes x 32 columns (19 populations, NB + D + 2
+    // site values, padding) in its warp's TMEM lane quadrant; one tile warp
+    // per quadrant
+    static constexpr uint32_t TCOLS = 64;
+    static_assert(!TM || (DFS && NINT <= 128 && NINT % 32 == 0), "TMEM hand-off: at most four full tile warps");
+    static_assert(!TM || Q + NSV <= 32, "site values fit one 32-column group");
     static constexpr uint32_t BBYTES = NB * BSLICE * 4;             // transaction bytes per variance slot
     static_assert((D == 3 ? 2 * SXB : SXB) <= 256 && SY <= 256, "TMA box edges are limited to 256 elements");
     static_assert(NT <= 1024, "too many threads");
@@ -93,6 +103,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     int xs[3], ys[3];    // x and y*nx of the sources x - e, y - e for e = -1, 0, 1
     int xo = 0;          // FX: bit e+1 set if source column x - e lies outside [0, nx)
     bool reservoir = false;
+    uint32_t tbase = 0;  // TM: TMEM base address of the block
 
     // Tile (bx, by) over march planes [pp0, pp1); bph carries the phase bits
     // of the variance-slot barriers from the block's previous segment.
@@ -133,6 +144,11 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         return reinterpret_cast<float*>(smem + Sh::OFF_SV) + (q & 1) * Sh::NSV * Sh::NINT + tid;
     }
     __device__ __forceinline__ int bs_of(int q) const { return (q - (p0 - 2)) % Sh::NBS; }
+    // TM: TMEM address of plane q's group in this thread's lane (lane
+    // quadrant of the warp in bits 16+, column offset in the low bits)
+    __device__ __forceinline__ uint32_t taddr(int q) const {
+        return tbase + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((q & 1) * 32);
+    }
     // DFS: populations of plane q for tile site t: population i at [i * NINT + t]
     __device__ __forceinline__ float* dfs(int q) const {
         return reinterpret_cast<float*>(smem + Sh::OFF_DF) + (q & 1) * Q * Sh::NINT + tid;
@@ -363,7 +379,21 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
         float omega, tau, T0;
         step_params(a, omega, tau, T0);
         site_moments<D, float>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
-        if (tile) {
+        if (Sh::TM && tile) {
+            // populations and site values of plane q to this thread's TMEM lane
+            float w[32];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) w[i] = df[i];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) w[Q + k] = bt[k];
+            w[Q + NB] = rho;
+#pragma unroll
+            for (int c = 0; c < D; ++c) w[Q + NB + 1 + c] = j[c];
+            w[Q + NB + 1 + D] = E;
+#pragma unroll
+            for (int k = Q + Sh::NSV; k < 32; ++k) w[k] = 0.0f;
+            tmem_st32(taddr(q), w);
+        } else if (tile) {
             if constexpr (Sh::DFS) {
                 float* dv = dfs(q);
 #pragma unroll
@@ -397,22 +427,38 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
                 return as + (rc + L::e(i, 0) + ((D == 3) ? RX * L::e(i, 1) : 0)) * NA2;
             },
             F, G);
-        const float* v = sv(p);
-        constexpr int NI = Sh::NINT;
-        float c_bt[NB], c_j[D];
-#pragma unroll
-        for (int k = 0; k < NB; ++k) c_bt[k] = v[k * NI];
-        const float c_rho = v[NB * NI];
-#pragma unroll
-        for (int c = 0; c < D; ++c) c_j[c] = v[(NB + 1 + c) * NI];
-        const float c_E = v[(NB + 1 + D) * NI];
+        float c_bt[NB], c_j[D], c_rho, c_E;
         float df[Q];
-        if constexpr (Sh::DFS) {
-            const float* dv = dfs(p);
+        if constexpr (Sh::TM) {
+            tmem_wait_st();  // this thread's store of plane p, an iteration ago
+            float w[32];
+            tmem_ld32(taddr(p), w);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) df[i] = dv[i * Sh::NINT];
+            for (int i = 0; i < Q; ++i) df[i] = w[i];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) c_bt[k] = w[Q + k];
+            c_rho = w[Q + NB];
+#pragma unroll
+            for (int c = 0; c < D; ++c) c_j[c] = w[Q + NB + 1 + c];
+            c_E = w[Q + NB + 1 + D];
         } else {
-            pull(p, zsp, df);  // second pull of the same values
+            const float* v = sv(p);
+            constexpr int NI = Sh::NINT;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) c_bt[k] = v[k * NI];
+            c_rho = v[NB * NI];
+#pragma unroll
+            for (int c = 0; c < D; ++c) c_j[c] = v[(NB + 1 + c) * NI];
+            c_E = v[(NB + 1 + D) * NI];
+        }
+        if constexpr (!Sh::TM) {
+            if constexpr (Sh::DFS) {
+                const float* dv = dfs(p);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) df[i] = dv[i * Sh::NINT];
+            } else {
+                pull(p, zsp, df);  // second pull of the same values
+            }
         }
         site_collide<D, FS, float, int, DiagDev<D + 2>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     }
@@ -423,10 +469,12 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
 // drained and the error flag raised; the caller leaves the kernel).
 template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX>
 __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* smem, int bx, int by, int p0,
-                                             int p1, DiagDev<D + 2>& acc, int& bad, uint32_t& bphase) {
+                                             int p1, DiagDev<D + 2>& acc, int& bad, uint32_t& bphase,
+                                             uint32_t tbase) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
     constexpr int NINT = Sh::NINT, NRING = Sh::NRING, RX = Sh::RX;
     FastBlock<D, FS, TX, TY, PFB, MB, FX> blk(ta, smem, bx, by, p0, p1, bphase);
+    blk.tbase = tbase;
     const int tid = threadIdx.x;
 
     // role of this thread: tile site (stage 1 + stage 2), ring site (stage 1)
@@ -528,7 +576,17 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
         for (int k = 0; k < Sh::NBS; ++k) mbar_init(bars + k, 1);
         fence_barrier_init();
     }
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Sh::OFF_TADDR);
+    if constexpr (Sh::TM) {
+        if (tid < 32) tmem_alloc(tslot, Sh::TCOLS);  // warp 0
+        tmem_fence_before_sync();
+    }
     __syncthreads();
+    uint32_t tbase = 0;
+    if constexpr (Sh::TM) {
+        tmem_fence_after_sync();
+        tbase = *tslot;
+    }
 
     DiagDev<D + 2> acc(float(D) * ta.s.T0_f);
     int bad = 0;
@@ -543,14 +601,26 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
             const int col = (int)(w / np);
             const int p0 = (int)(w - (long long)col * np);
             const int p1 = (int)min((long long)np, p0 + (w1 - w));
-            ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, col % ncx, col / ncx, p0, p1, acc, bad, bphase);
+            ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, col % ncx, col / ncx, p0, p1, acc, bad, bphase,
+                                                          tbase);
             w += p1 - p0;
         }
     } else {
         const int np = (D == 3) ? ta.s.nz : ta.s.ny;
         const int p0 = blockIdx.z * ta.s.chunk;
         ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, blockIdx.x, blockIdx.y, p0,
-                                                       min(p0 + ta.s.chunk, np), acc, bad, bphase);
+                                                       min(p0 + ta.s.chunk, np), acc, bad, bphase, tbase);
+    }
+    if constexpr (Sh::TM) {
+        // every thread's TMEM stores complete, then warp 0 frees the columns
+        // (on the abort path too: the segment left with every thread)
+        tmem_wait_st();
+        tmem_fence_before_sync();
+        __syncthreads();
+        if (tid < 32) {
+            tmem_fence_after_sync();
+            tmem_dealloc(tbase, Sh::TCOLS);
+        }
     }
     if (!ok) return;
     if (bad) atomicOr(ta.s.flag, bad);
