@@ -269,8 +269,7 @@ std::vector<int> chunk_candidates(const lbm_sim* s) {
 }
 
 lbm_status ensure_partial(lbm_sim* s, int v, int chunk) {
-    // at least 8 blocks per multiprocessor: the persistent step grids
-    size_t nb = std::max(blocks_of(s, v, chunk), (size_t)8 * device_sms());
+    size_t nb = blocks_of(s, v, chunk);
     if (nb <= s->partial_blocks) return LBM_OK;
     double* p = (double*)s->dalloc(nb * (s->D + 2) * sizeof(double));
     if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");

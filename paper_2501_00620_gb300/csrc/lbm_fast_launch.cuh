@@ -10,28 +10,28 @@
 namespace lbm {
 
 // Tile TX x TY, PFB flags (bit 0: extra variance plane in flight, bit 1:
-// populations to stage 2 through shared memory), resident blocks per SM MB,
-// persistent grid (balanced shares of the column x plane work) or one block
-// per (tile, chunk).
+// populations to stage 2 through shared memory, bit 2: that hand-off in
+// tensor memory), resident blocks per SM MB.
 struct FastVariant {
-    int tx, ty, pfb, mb, persist;
+    int tx, ty, pfb, mb;
 };
 
 // D3Q19: 32 x 8 at two blocks per SM; 32 x 4 at three; 32 x 4 with one more
 // variance plane in flight and the populations handed to stage 2 through
 // shared memory, at two blocks per SM; 32 x 4 with one more variance plane
-// in flight at three; the third with the hand-off in tensor memory at three.
-constexpr FastVariant kFast3[] = {{32, 8, 0, 2, 0}, {32, 4, 0, 3, 0}, {32, 4, 3, 2, 0}, {32, 4, 1, 3, 0},
-                                  {32, 4, 7, 3, 0}};
-// D2Q9: strips of 128 or 64 sites; 128 with the populations handed to
-// stage 2 through shared memory; 128 persistent.
-constexpr FastVariant kFast2[] = {{128, 1, 0, 5, 0}, {128, 1, 1, 5, 0}, {128, 1, 3, 5, 0}, {128, 1, 0, 5, 1}};
+// in flight at three; the third with the hand-off in tensor memory at three;
+// 32 x 8 with the hand-off in tensor memory at two.
+constexpr FastVariant kFast3[] = {{32, 8, 0, 2}, {32, 4, 0, 3}, {32, 4, 3, 2}, {32, 4, 1, 3},
+                                  {32, 4, 7, 3}, {32, 8, 7, 2}};
+// D2Q9: strips of 128 sites; with the populations handed to stage 2 through
+// shared memory; with that hand-off in tensor memory at six blocks per SM.
+constexpr FastVariant kFast2[] = {{128, 1, 0, 5}, {128, 1, 1, 5}, {128, 1, 3, 5}, {128, 1, 7, 6}};
 
 
-template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX, bool PERSIST>
+template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX>
 cudaError_t launch_fast(const TmaArgs& ta, cudaStream_t st) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
-    auto kern = step_fast_kernel<D, FS, TX, TY, PFB, MB, FX, PERSIST>;
+    auto kern = step_fast_kernel<D, FS, TX, TY, PFB, MB, FX>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
@@ -41,10 +41,6 @@ cudaError_t launch_fast(const TmaArgs& ta, cudaStream_t st) {
     const StepArgs& a = ta.s;
     const int np = D == 3 ? a.nz : a.ny;
     dim3 grid(a.nx / TX, D == 3 ? a.ny / TY : 1, (np + a.chunk - 1) / a.chunk);
-    if (PERSIST) {
-        const long long work = (long long)grid.x * grid.y * np;
-        grid = dim3((unsigned)std::min<long long>(work, (long long)device_sms() * MB), 1, 1);
-    }
     kern<<<grid, Sh::NT, Sh::SMEM, st>>>(ta);
     return cudaGetLastError();
 }
@@ -67,7 +63,7 @@ void fast_box(TmaBox* b) {
             fast_box<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb>(box);                          \
             return cudaSuccess;                                                                         \
         }                                                                                               \
-        return launch_fast<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb, FX, (TAB[K].persist != 0)>(*ta, st);
+        return launch_fast<D, FS, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb, FX>(*ta, st);
 
 template <int D, typename FS, bool FX>
 cudaError_t fast_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t st) {
@@ -78,6 +74,7 @@ cudaError_t fast_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t 
             LBM_FAST_CASE(3, kFast3, 2)
             LBM_FAST_CASE(3, kFast3, 3)
             LBM_FAST_CASE(3, kFast3, 4)
+            LBM_FAST_CASE(3, kFast3, 5)
             default: return cudaErrorInvalidValue;
         }
     } else {

@@ -72,10 +72,11 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr int OFF_TADDR = OFF_BAR + NBS * 8;               // TM: TMEM base address
     static constexpr int SMEM = OFF_TADDR + 16;
     // TM: per tile thread 2 planes x 32 columns (19 populations, NB + D + 2
-    // site values, padding) in its warp's TMEM lane quadrant; one tile warp
-    // per quadrant
-    static constexpr uint32_t TCOLS = 64;
-    static_assert(!TM || (DFS && NINT <= 128 && NINT % 32 == 0), "TMEM hand-off: at most four full tile warps");
+    // site values, padding) in its warp's TMEM lane quadrant (warp % 4);
+    // tile warps sharing a quadrant take consecutive 64-column groups
+    static constexpr int TGROUPS = (NINT / 32 + 3) / 4;
+    static constexpr uint32_t TCOLS = TGROUPS <= 1 ? 64u : (TGROUPS <= 2 ? 128u : 256u);
+    static_assert(!TM || (DFS && NINT % 32 == 0 && TGROUPS <= 4), "TMEM hand-off: whole tile warps, <= 16");
     static_assert(!TM || Q + NSV <= 32, "site values fit one 32-column group");
     static constexpr uint32_t BBYTES = NB * BSLICE * 4;             // transaction bytes per variance slot
     static_assert((D == 3 ? 2 * SXB : SXB) <= 256 && SY <= 256, "TMA box edges are limited to 256 elements");
@@ -147,7 +148,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     // TM: TMEM address of plane q's group in this thread's lane (lane
     // quadrant of the warp in bits 16+, column offset in the low bits)
     __device__ __forceinline__ uint32_t taddr(int q) const {
-        return tbase + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((q & 1) * 32);
+        return tbase + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * 64 + (q & 1) * 32);
     }
     // DFS: populations of plane q for tile site t: population i at [i * NINT + t]
     __device__ __forceinline__ float* dfs(int q) const {
@@ -559,13 +560,8 @@ __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* s
     return true;
 }
 
-// Grid: (nx/TX, ny/TY, chunks) with one segment per block, or, with PERSIST,
-// a one-dimensional grid of about the resident block count in which block b
-// takes the b-th equal share of the (tile column, plane) work in column-major
-// order -- a contiguous run of planes of one or two columns -- so that the
-// load is balanced without a tail wave and each block restarts its march at
-// most once or twice.
-template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX, bool PERSIST>
+// Grid: (nx/TX, ny/TY, chunks), one segment of the march per block.
+template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX>
 __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
     step_fast_kernel(const __grid_constant__ TmaArgs ta) {
     using Sh = FastShape<D, FS, TX, TY, PFB, MB>;
@@ -591,26 +587,10 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
     DiagDev<D + 2> acc(float(D) * ta.s.T0_f);
     int bad = 0;
     uint32_t bphase = 0;
-    bool ok = true;
-    if constexpr (PERSIST) {
-        const int np = (D == 3) ? ta.s.nz : ta.s.ny;
-        const int ncx = ta.s.nx / TX;
-        const long long W = (long long)ncx * ((D == 3) ? ta.s.ny / TY : 1) * np;
-        const long long w1 = W * (blockIdx.x + 1) / gridDim.x;
-        for (long long w = W * blockIdx.x / gridDim.x; ok && w < w1;) {
-            const int col = (int)(w / np);
-            const int p0 = (int)(w - (long long)col * np);
-            const int p1 = (int)min((long long)np, p0 + (w1 - w));
-            ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, col % ncx, col / ncx, p0, p1, acc, bad, bphase,
-                                                          tbase);
-            w += p1 - p0;
-        }
-    } else {
-        const int np = (D == 3) ? ta.s.nz : ta.s.ny;
-        const int p0 = blockIdx.z * ta.s.chunk;
-        ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, blockIdx.x, blockIdx.y, p0,
-                                                       min(p0 + ta.s.chunk, np), acc, bad, bphase, tbase);
-    }
+    const int np = (D == 3) ? ta.s.nz : ta.s.ny;
+    const int p0 = blockIdx.z * ta.s.chunk;
+    const bool ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, blockIdx.x, blockIdx.y, p0,
+                                                             min(p0 + ta.s.chunk, np), acc, bad, bphase, tbase);
     if constexpr (Sh::TM) {
         // every thread's TMEM stores complete, then warp 0 frees the columns
         // (on the abort path too: the segment left with every thread)
