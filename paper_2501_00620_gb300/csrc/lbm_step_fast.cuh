@@ -68,7 +68,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr int OFF_SV = OFF_AUX + round_up(NAS * NA2 * 8 * RS, 16);
     static constexpr int OFF_DF = OFF_SV + (TM ? 0 : 2 * NSV * NINT * 4);  // DFS: [2][Q][NINT] populations
     static constexpr int OFF_RED = OFF_DF + (DFS && !TM ? 2 * Q * NINT * 4 : 0);
-    static constexpr int OFF_BAR = OFF_RED + 32 * (D + 2) * 8;
+    static constexpr int OFF_BAR = OFF_RED + (NT / 32) * (D + 2) * 8;  // per-warp diagnostics partials
     static constexpr int OFF_TADDR = OFF_BAR + NBS * 8;               // TM: TMEM base address
     static constexpr int SMEM = OFF_TADDR + 16;
     // TM: per tile thread 2 planes x 32 columns (19 populations, NB + D + 2
