@@ -54,7 +54,7 @@ struct ServeSim {
 };
 
 using Sh1 = StepShape<1, float, kTX, 1>;
-using ShS = StripShape<float, kTX>;
+using ShS = StripShape<float, kTX, true>;  // the serve kernel is register-bound: hand populations over
 static_assert(kTX == kStripNT, "the strip body runs on the serve kernel's blocks");
 constexpr size_t kSmem = Sh1::smem > (size_t)ShS::SMEM ? Sh1::smem : (size_t)ShS::SMEM;
 
@@ -86,9 +86,9 @@ __global__ void __launch_bounds__(kTX, 2) serve_kernel(const ServeSim* __restric
                 DiagDev<4> acc(0.0f);  // unused: no diagnostics in serving rounds
                 int bad = 0;
                 if (a.fixed_x)
-                    strip_block<float, kTX, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+                    strip_block<float, kTX, true, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
                 else
-                    strip_block<float, kTX, false>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+                    strip_block<float, kTX, false, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
                 if (bad) atomicOr(a.flag, bad);
             }
             __syncthreads();  // the next work item reuses shared memory

@@ -14,7 +14,7 @@
 //   stored after it, so their latency overlaps stage 1.
 // * (u0, rho b) of the strip and ring live in four shared row slots; tile
 //   sites hand their site values to stage 2 through two shared slots and
-//   pull their populations a second time in stage 2.
+//   either pull their populations again or (HANDOFF) hand those over too.
 // * FX selects the fixed-state boundary in x (frozen reservoirs).
 #pragma once
 
@@ -22,7 +22,10 @@
 
 namespace lbm {
 
-template <typename FS, int NT> struct StripShape {
+// HANDOFF: tile sites hand their pulled populations to stage 2 through
+// shared memory (18 KB more) instead of pulling them again -- a gain where
+// registers, not shared memory, bound the blocks per SM (the serving kernel).
+template <typename FS, int NT, bool HANDOFF = false> struct StripShape {
     static constexpr int Q = 9, NB = 3, NA2 = 3;
     static constexpr int TX = NT - 2;    // tile sites of a full strip
     static constexpr int BW = NT + 2;    // staged variance row: x from x0 - 2
@@ -30,18 +33,19 @@ template <typename FS, int NT> struct StripShape {
     static constexpr int NSV = NB + 2 + 2;  // bbar, rho, j0 (2), Ebar
     static constexpr int OFF_AUX = round_up(NBS * NB * BW * 4, 16);
     static constexpr int OFF_SV = OFF_AUX + NAS * NT * NA2 * 8;
-    static constexpr int OFF_RED = OFF_SV + 2 * NSV * NT * 4;
+    static constexpr int OFF_DF = OFF_SV + 2 * NSV * NT * 4;  // [2][Q][NT] populations of tile sites
+    static constexpr int OFF_RED = OFF_DF + (HANDOFF ? 2 * Q * NT * 4 : 0);
     static constexpr int SMEM = OFF_RED + 32 * 4 * 8;
     static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
 };
 
 // One strip (bx) over march rows [bz*chunk, bz*chunk + chunk) of the lattice
 // in `a`.  Every thread of the block calls it; it contains block barriers.
-template <typename FS, int NT, bool FX>
+template <typename FS, int NT, bool FX, bool HANDOFF = false>
 __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, unsigned char* smem,
                                             DiagDev<4>& acc, int& bad) {
     using L = Lattice<2>;
-    using Sh = StripShape<FS, NT>;
+    using Sh = StripShape<FS, NT, HANDOFF>;
     constexpr int Q = Sh::Q, NB = Sh::NB, NA2 = Sh::NA2, BW = Sh::BW;
     const int tid = threadIdx.x;
     const int nx = a.nx, np = a.ny, Ni = (int)a.N, rows = (int)a.rows;
@@ -83,6 +87,8 @@ __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, u
     auto bslot = [&](int r) { return bslots + ((r - (p0 - 2)) & 3) * (NB * BW); };
     auto aux = [&](int q) { return auxs + ((q - p0 + 1) & 3) * (NT * NA2); };
     auto sv = [&](int q) { return svs + (q & 1) * (Sh::NSV * NT) + tid; };
+    float* dfbase = reinterpret_cast<float*>(smem + Sh::OFF_DF);
+    auto dfs = [&](int q) { return dfbase + (q & 1) * (Q * NT) + tid; };
 
     // variance of row r at staged positions c = tid, tid + NT (x = x0 - 2 + c)
     const float* __restrict__ bin = static_cast<const float*>(a.bin);
@@ -177,6 +183,11 @@ __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, u
         float u0[2], rb[NB], bt[NB], rho, j[2], E;
         site_moments<2, float>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
         if (interior) {
+            if constexpr (HANDOFF) {
+                float* dv = dfs(q);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) dv[i * NT] = df[i];
+            }
             float* v = sv(q);
 #pragma unroll
             for (int k = 0; k < NB; ++k) v[k * NT] = bt[k];
@@ -212,7 +223,13 @@ __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, u
         c_j[1] = v[(NB + 2) * NT];
         const float c_E = v[(NB + 3) * NT];
         float df[Q];
-        pull(p, df);  // second pull of the same values
+        if constexpr (HANDOFF) {
+            const float* dv = dfs(p);  // the populations stage 1 pulled
+#pragma unroll
+            for (int i = 0; i < Q; ++i) df[i] = dv[i * NT];
+        } else {
+            pull(p, df);  // second pull of the same values
+        }
         const int s = gxw + nx * wrapq(p);
         site_collide<2, FS, float, int, DiagDev<4>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     };
