@@ -175,16 +175,40 @@ def hbm_peak():
 
 
 KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_tma.cuh",
-                  "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
+                  "lbm_lean.cuh", "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
+
+
+def _code_only(text):
+    """C++ source without // and /* */ comments and blank lines: edits of
+    comments do not change what is compiled."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
 
 
 def kernel_source_hash():
-    """Hash of the device sources the step kernels are built from: an ncu
-    figure taken from other sources no longer describes the kernel."""
+    """Hash of the code (comments stripped) of the device sources the step
+    kernels are built from: an ncu figure taken from other code no longer
+    describes the kernel."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2501_00620_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2501_00620_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

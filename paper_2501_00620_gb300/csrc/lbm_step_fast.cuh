@@ -5,22 +5,29 @@
 // the data movement and the instruction selection differ.
 //
 // * Populations are pulled straight from global memory (read-only path) with
-//   32-bit offsets from per-plane base pointers.  The pull is a permutation --
-//   every emitted value is read by exactly one site -- so staging them in
-//   shared memory would buy no reuse.
+//   32-bit offsets from per-plane base pointers, after one bulk tensor
+//   prefetch per block and plane has brought them into L2.  The pull is a
+//   permutation -- every emitted value is read by exactly one site -- so
+//   staging them in shared memory would buy no reuse.
 // * The variance planes, which the mass-weighted transport (Eq. 66) reads at
 //   all Q neighbours, are staged by tiled bulk tensor copies (TMA) in a ring
 //   of 3 + PF plane slots (PF = PFB & 1).  In 3D they are stored as component
-//   pairs, so the transport reads one 8-byte pair per neighbour and accumulates it with the
-//   packed FP32x2 multiply-add of sm_100+ (two FP32 FMAs per instruction).
+//   pairs, so the transport reads one 8-byte pair per neighbour and
+//   accumulates it with the packed FP32x2 multiply-add of sm_100+ (two FP32
+//   FMAs per instruction).
 // * (u0, rho b) of the tile plus a one-site ring live in four shared plane
 //   slots, site-major as float2 pairs grouped by the rows of rho b that a
 //   neighbour direction needs; the gradient (Eqs. 59, 61) loads only those
 //   pairs, folds the sign of e_i into the adds, and applies the lattice
 //   weights once at the end (axis terms first, scaled by w_axis / w_edge).
-// * A tile site hands (bbar, rho, j0, Ebar) from stage 1 to stage 2 through
-//   its own column of two shared slots (plane parity) and pulls its
-//   populations a second time in stage 2.
+// * A tile site hands (bbar, rho, j0, Ebar) from stage 1 to stage 2 and,
+//   depending on PFB, either pulls its populations a second time or hands
+//   them over too: through two shared slots (plane parity), or through its
+//   own lane of tensor memory (tcgen05.st / tcgen05.ld), which the path
+//   leaves otherwise unused and which does not count against the shared
+//   memory that limits the blocks per SM.
+// * Halo items of edge blocks (periodic images or reservoirs) are assigned
+//   one per thread with their geometry computed once per block.
 // * The conservation diagnostics are summed per thread in FP32 as deviations
 //   from the rest state (rho - 1, E - D T0), which keeps the per-thread sums
 //   small and exact to far below the storage rounding; blocks reduce in FP64.
