@@ -58,6 +58,7 @@ def lib():
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
         L.orc_nstep.argtypes = [ctypes.c_void_p]
         L.orc_nstep.restype = ctypes.c_long
+        L.orc_set_force.argtypes = [ctypes.c_void_p, dp]
         L.orc_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
         L.orc_diagnostics.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_emitted.argtypes = [ctypes.c_void_p, dp, dp]
@@ -141,7 +142,7 @@ class Sim:
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.Q, self.nb = n_q(d), n_b(d)
-        bcode = {"periodic": 0, "fixed": 1}[bc]
+        bcode = {"periodic": 0, "fixed": 1, "walls": 2}[bc]
         self._h = lib().orc_create(d, nx, ny, nz, float(tau), float(T0),
                                    int(bool(thermal)), bcode)
         if not self._h:
@@ -162,6 +163,12 @@ class Sim:
 
     def step(self, n=1):
         lib().orc_step(self._h, int(n))
+
+    def set_force(self, a):
+        """Uniform body-force acceleration (d components)."""
+        aa = np.zeros(3)
+        aa[:self.d] = np.asarray(a, dtype=np.float64)[:self.d]
+        lib().orc_set_force(self._h, _p(aa))
 
     @property
     def nstep(self):

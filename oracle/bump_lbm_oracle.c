@@ -57,6 +57,22 @@
  *       [0, nx) are frozen equilibrium reservoirs carrying the initial state of
  *       the edge site of their row.  They emit f^eq / b^eq of that state and
  *       present rho*b = rho b^eq and u0 = u to the gradient stencil.
+ *   R9  Walls (Sec. III.A uses half-step bounce-back walls [Ladd 1994]): two
+ *       stationary walls normal to the last axis (y in 2D, z in 3D), half a
+ *       site outside the lattice, at -1/2 and n - 1/2; the other axes stay
+ *       periodic.  A population whose source x - e_i lies beyond a wall is the
+ *       one the site itself emitted in the opposite direction, fbar*_-i(x),
+ *       and it carries that site's bbar*(x) in the transport of Eq. 66.  The
+ *       gradient stencil sees, one site beyond a wall, the image of the fluid
+ *       site facing it across the wall: the same rho*b and the reversed u0
+ *       (bounce-back reverses velocities and leaves the variance unchanged).
+ *   R10 Body force (Sec. III.A drives Poiseuille flow by a uniform
+ *       acceleration a): the force density rho a joins the gradient force,
+ *       F -> F + rho a, and its second-moment source joins G,
+ *       G_bc -> G_bc + rho (u_b a_c + u_c a_b) with the corrected velocity
+ *       u = (j0 + F/2)/rho of Eq. 57, so that the forcing projection (R5)
+ *       carries both and, in a uniform flow, the work of the force goes into
+ *       kinetic energy alone (the thermal T stays constant).
  *
  * Weights w_i = f^eq_i(rho=1, u=0), cs2 = c^2/3 = 1/3.
  */
@@ -73,6 +89,7 @@
 typedef struct {
     int d, Q, nb;
     int e[QMAX][3];
+    int opp[QMAX];             /* index of -e_i */
     double w[QMAX];
 } orc_lattice;
 
@@ -81,7 +98,8 @@ typedef struct {
     int nx, ny, nz;
     long N;
     double tau, T0, omega;
-    int thermal, bc;           /* bc: 0 periodic, 1 fixed-state in x */
+    int thermal, bc;           /* bc: 0 periodic, 1 fixed-state in x, 2 walls (R9) */
+    double acc[3];             /* uniform body-force acceleration (R10) */
     long nstep;
     /* state at time t (pre-collision, post-stream) */
     double *f, *b;
@@ -226,6 +244,9 @@ static void lattice_init(orc_lattice *L, int d)
         for (int a = 0; a < 3; ++a) L->e[i][a] = E[i][a];
         L->w[i] = w[i];
     }
+    for (int i = 0; i < L->Q; ++i)
+        for (int j = 0; j < L->Q; ++j)
+            if (E[j][0] == -E[i][0] && E[j][1] == -E[i][1] && E[j][2] == -E[i][2]) L->opp[i] = j;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -235,6 +256,11 @@ static void lattice_init(orc_lattice *L, int d)
 static long neighbour(const orc_sim *s, int x, int y, int z, int sx, int sy, int sz)
 {
     int X = x + sx, Y = y + sy, Z = z + sz;
+    if (s->bc == 2) {           /* walls: callers resolve the wall axis first */
+        X = ((X % s->nx) + s->nx) % s->nx;
+        if (s->L.d == 3) Y = ((Y % s->ny) + s->ny) % s->ny;
+        return (long)X + (long)s->nx * ((long)Y + (long)s->ny * Z);
+    }
     Y = ((Y % s->ny) + s->ny) % s->ny;
     Z = ((Z % s->nz) + s->nz) % s->nz;
     if (s->bc == 1 && (X < 0 || X >= s->nx)) {
@@ -244,6 +270,26 @@ static long neighbour(const orc_sim *s, int x, int y, int z, int sx, int sy, int
     }
     X = ((X % s->nx) + s->nx) % s->nx;
     return (long)X + (long)s->nx * ((long)Y + (long)s->ny * Z);
+}
+
+/* Coordinate along the wall axis (R9) of (x,y,z) and its extent.          */
+static int wall_coord(const orc_sim *s, int y, int z) { return s->L.d == 3 ? z : y; }
+static int wall_extent(const orc_sim *s) { return s->L.d == 3 ? s->nz : s->ny; }
+
+/* Gradient-stencil neighbour (x,y,z) + e under the walls of R9: the fluid
+ * site facing it across the wall, with *sign = -1 for the reversed u0.      */
+static long grad_neighbour(const orc_sim *s, int x, int y, int z, const int *e, double *sign)
+{
+    *sign = 1.0;
+    if (s->bc != 2) return neighbour(s, x, y, z, e[0], e[1], e[2]);
+    int X = x + e[0], Y = y + e[1], Z = z + e[2];
+    int w = wall_coord(s, Y, Z), n = wall_extent(s);
+    if (w < 0 || w >= n) {
+        int m = w < 0 ? -1 - w : 2 * n - 1 - w;      /* mirror across the wall */
+        if (s->L.d == 3) Z = m; else Y = m;
+        *sign = -1.0;
+    }
+    return neighbour(s, X, Y, Z, 0, 0, 0);
 }
 
 static void site_coords(const orc_sim *s, long n, int *x, int *y, int *z)
@@ -303,7 +349,8 @@ static double grad_rb(const orc_sim *s, int x, int y, int z, int a, int k)
     double acc = 0.0;
     for (int i = 1; i < L->Q; ++i) {
         if (L->e[i][a] == 0) continue;
-        long m = neighbour(s, x, y, z, L->e[i][0], L->e[i][1], L->e[i][2]);
+        double sg;
+        long m = grad_neighbour(s, x, y, z, L->e[i], &sg);
         acc += L->w[i] * L->e[i][a] * rb_at(s, m)[k];
     }
     return 3.0 * acc;
@@ -316,9 +363,10 @@ static double grad_H(const orc_sim *s, int x, int y, int z, int a, int bb, int c
     double acc = 0.0;
     for (int i = 1; i < L->Q; ++i) {
         if (L->e[i][a] == 0) continue;
-        long m = neighbour(s, x, y, z, L->e[i][0], L->e[i][1], L->e[i][2]);
+        double sg;
+        long m = grad_neighbour(s, x, y, z, L->e[i], &sg);
         const double *u = u0_at(s, m), *r = rb_at(s, m);
-        double H = u[c] * r[comp_index(d, a, bb)] + u[bb] * r[comp_index(d, c, a)];
+        double H = sg * (u[c] * r[comp_index(d, a, bb)] + u[bb] * r[comp_index(d, c, a)]);
         acc += L->w[i] * L->e[i][a] * H;
     }
     return 3.0 * acc;
@@ -344,6 +392,14 @@ static void corrected_moments(const orc_sim *s, long n, double *F, double *G,
             G[comp_index(d, bb, c)] = -acc;
         }
     double rho = s->rho[n], uu = 0.0, trG = 0.0;
+    /* body force (R10): F + rho a, then G + rho (u a + a u) with the
+     * corrected momentum rho u = j0 + F/2 of Eq. 57 */
+    double ru[3] = {0.0, 0.0, 0.0};
+    for (int bb = 0; bb < d; ++bb) F[bb] += rho * s->acc[bb];
+    for (int bb = 0; bb < d; ++bb) ru[bb] = s->j0[n * 3 + bb] + 0.5 * F[bb];
+    for (int bb = 0; bb < d; ++bb)
+        for (int c = bb; c < d; ++c)
+            G[comp_index(d, bb, c)] += ru[bb] * s->acc[c] + ru[c] * s->acc[bb];
     for (int a = 0; a < 3; ++a) u[a] = 0.0;
     for (int a = 0; a < d; ++a) {
         u[a] = (s->j0[n * 3 + a] + 0.5 * F[a]) / rho;     /* Eq. 57 */
@@ -392,9 +448,18 @@ static void phase_c(orc_sim *s)
         double rho1 = 0.0, rbb[NBMAX];
         for (int k = 0; k < nb; ++k) rbb[k] = 0.0;
         for (int i = 0; i < Q; ++i) {
-            long m = neighbour(s, x, y, z, -L->e[i][0], -L->e[i][1], -L->e[i][2]);
-            double fi = fs_at(s, m)[i];
-            const double *bm = bs_at(s, m);
+            double fi;
+            const double *bm;
+            int w = wall_coord(s, y - L->e[i][1], z - L->e[i][2]);
+            if (s->bc == 2 && (w < 0 || w >= wall_extent(s))) {
+                /* half-way bounce-back (R9): the site's own opposite emission */
+                fi = s->fs[n * Q + L->opp[i]];
+                bm = s->bs + n * nb;
+            } else {
+                long m = neighbour(s, x, y, z, -L->e[i][0], -L->e[i][1], -L->e[i][2]);
+                fi = fs_at(s, m)[i];
+                bm = bs_at(s, m);
+            }
             s->f[n * Q + i] = fi;
             rho1 += fi;
             for (int k = 0; k < nb; ++k) rbb[k] += fi * bm[k];
@@ -455,6 +520,7 @@ void *orc_create(int d, int nx, int ny, int nz, double tau, double T0, int therm
 {
     if (d < 1 || d > 3 || nx < 1 || ny < 1 || nz < 1 || !(tau > 0) || !(T0 > 0)) return NULL;
     if ((d < 2 && ny != 1) || (d < 3 && nz != 1)) return NULL;
+    if (bc < 0 || bc > 2 || (bc == 2 && d < 2)) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     lattice_init(&s->L, d);
     s->nx = nx; s->ny = ny; s->nz = nz;
@@ -520,6 +586,13 @@ void orc_step(void *h, long nsteps)
 }
 
 long orc_nstep(void *h) { return ((orc_sim *)h)->nstep; }
+
+/* Uniform body-force acceleration (R10), d components.                    */
+void orc_set_force(void *h, const double *a)
+{
+    orc_sim *s = (orc_sim *)h;
+    for (int c = 0; c < 3; ++c) s->acc[c] = c < s->L.d ? a[c] : 0.0;
+}
 
 /* rho, corrected u (d planes) and the moment temperature at the current t */
 void orc_moments(void *h, double *rho, double *u, double *T)
