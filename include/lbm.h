@@ -62,9 +62,18 @@ typedef enum {
 
 typedef enum {
     LBM_BC_PERIODIC = 0,    /* periodic on every axis */
-    LBM_BC_FIXED_STATE = 1  /* x: frozen equilibrium reservoirs carrying the
+    LBM_BC_FIXED_STATE = 1, /* x: frozen equilibrium reservoirs carrying the
                                initial state of the edge site of each row;
                                y and z periodic */
+    LBM_BC_WALLS = 2        /* dim 2, 3: two stationary half-way bounce-back
+                               walls (Sec. III.A) normal to the last axis (y in
+                               2D, z in 3D), half a site outside the lattice;
+                               the other axes periodic.  A population whose
+                               source lies beyond a wall is the site's own
+                               emission in the opposite direction, with the
+                               site's bbar; the gradient stencil sees beyond a
+                               wall the image of the facing site (same rho b,
+                               reversed u0).  Runs on the generic kernel. */
 } lbm_bc;
 
 typedef enum {
@@ -135,6 +144,16 @@ typedef struct {
  * reservoirs take the state of the edge site of each row.  Resets the step
  * counter.  Blocks until the copy is done. */
 lbm_status lbm_init(lbm_sim *sim, const lbm_fields_in *fields);
+
+/* Uniform body force (Sec. III.A drives Poiseuille flow by an acceleration):
+ * `a` points at dim host doubles, the acceleration in lattice units (copied;
+ * NULL or all zeros removes the force).  Each step adds the force density
+ * rho a to the gradient force F (Eq. 59) and rho (u a + a u) to G (Eq. 61),
+ * with the corrected u = (j0 + F/2)/rho of Eq. 57, before the collision; so
+ * the reported u and the momentum diagnostic carry half a step of force.
+ * A forced simulation runs on the generic kernel.  Waits for the
+ * simulation's stream.  LBM_EINVAL for a NULL sim or a non-finite value. */
+lbm_status lbm_set_force(lbm_sim *sim, const double *a);
 
 /* Advance n >= 0 time steps (Sec. II.C, Eqs. 49-68): asynchronous on the
  * simulation's stream. */

@@ -29,7 +29,15 @@ struct StepArgs {
     int hist_cap;
     long long* step_ctr;  // device step counter (history index)
     int* flag;            // bit 0: fatal (rho <= 0 or non-finite); bit 1: T <= 0 seen
+    int walls;            // 1: half-way bounce-back walls normal to the march axis (D = 2, 3)
+    int forced;           // 1: uniform body force of acceleration acc
+    double acc[3];        // body-force acceleration (lattice units)
+    float acc_f[3];       // the same, rounded to FP32 on the host
 };
+
+// Body-force acceleration in the arithmetic type R.
+__host__ __device__ __forceinline__ double acc_param(const StepArgs& a, int c, double) { return a.acc[c]; }
+__host__ __device__ __forceinline__ float acc_param(const StepArgs& a, int c, float) { return a.acc_f[c]; }
 
 // omega, tau, T0 in the arithmetic type R (no per-site conversion from FP64).
 __host__ __device__ __forceinline__ void step_params(const StepArgs& a, double& omega, double& tau, double& T0) {

@@ -10,6 +10,7 @@
 #include <array>
 #include <chrono>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -63,6 +64,8 @@ struct lbm_sim {
     long long N = 0, rows = 0;
     double tau = 0, T0 = 0;
     int bc = 0;
+    double acc[3] = {0, 0, 0};  // body-force acceleration
+    bool forced = false;
     lbm_opts opts{};
     int dtype = 0;
     int device = 0;
@@ -134,6 +137,12 @@ StepArgs base_args(const lbm_sim* s) {
     set_step_params(a, s->tau, s->T0);
     a.thermal = s->opts.thermal;
     a.fixed_x = s->bc == LBM_BC_FIXED_STATE;
+    a.walls = s->bc == LBM_BC_WALLS;
+    a.forced = s->forced ? 1 : 0;
+    for (int c = 0; c < 3; ++c) {
+        a.acc[c] = s->acc[c];
+        a.acc_f[c] = (float)s->acc[c];
+    }
     a.rows = s->rows;
     a.gf = s->gf;
     a.gb = s->gb;
@@ -162,10 +171,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// Walls and the body force are implemented in the generic kernel only: the
+// staged, strip and serving kernels serve periodic and fixed-state lattices.
+bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced; }
+bool variant_allowed(const lbm_sim* s, int v) {
+    if (!generic_only(s)) return true;
+    return v < kTmaBase && !(s->D == 2 && v == 3);
+}
+
 // The TMA-staged kernel needs FP32/16-bit storage, tiles that divide the
 // extents, and rows whose byte length is a multiple of 16 (tensor strides).
 bool tma_applicable(const lbm_sim* s, int v) {
-    if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64) return false;
+    if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64 || generic_only(s)) return false;
     if (v - kTmaBase >= n_tma_variants(s->D)) return false;
     Variant t = variant(s->D, v);
     if (s->nx % t.tx != 0) return false;
@@ -404,7 +421,7 @@ lbm_status tune_multi(lbm_sim* s) {
 }
 
 lbm_status autotune(lbm_sim* s) {
-    auto key = std::make_tuple(s->D, s->dtype, s->nx, s->ny, s->nz);
+    auto key = std::make_tuple(s->D, s->dtype * 2 + (generic_only(s) ? 1 : 0), s->nx, s->ny, s->nz);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune.find(key);
@@ -416,10 +433,12 @@ lbm_status autotune(lbm_sim* s) {
     }
     int nv = n_variants(s->D);
     std::vector<int> vars;
-    if (s->opts.tile >= 0 && (s->opts.tile < nv || tma_applicable(s, s->opts.tile))) {
+    if (s->opts.tile >= 0 && variant_allowed(s, s->opts.tile) &&
+        (s->opts.tile < nv || tma_applicable(s, s->opts.tile))) {
         vars.push_back(s->opts.tile);
     } else {
-        for (int v = 0; v < nv; ++v) vars.push_back(v);
+        for (int v = 0; v < nv; ++v)
+            if (variant_allowed(s, v)) vars.push_back(v);
         for (int k = 0; k < n_tma_variants(s->D); ++k)
             if (tma_applicable(s, kTmaBase + k)) vars.push_back(kTmaBase + k);
     }
@@ -556,7 +575,9 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
     if (nx < 1 || ny < 1 || nz < 1) return fail(LBM_EINVAL, "extents must be >= 1");
     if ((dim < 2 && ny != 1) || (dim < 3 && nz != 1)) return fail(LBM_EINVAL, "unused extents must be 1");
     if (!(tau > 0) || !(T0 > 0)) return fail(LBM_EINVAL, "tau and T0 must be > 0");
-    if (bc != LBM_BC_PERIODIC && bc != LBM_BC_FIXED_STATE) return fail(LBM_EINVAL, "unknown boundary");
+    if (bc != LBM_BC_PERIODIC && bc != LBM_BC_FIXED_STATE && bc != LBM_BC_WALLS)
+        return fail(LBM_EINVAL, "unknown boundary");
+    if (bc == LBM_BC_WALLS && dim < 2) return fail(LBM_EINVAL, "walls need dim 2 or 3");
     lbm_opts o;
     if (opts)
         o = *opts;
@@ -672,6 +693,31 @@ lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
     CK(cudaMemsetAsync(s->ticket, 0, 64, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->nstep = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_sim* s, const double* a) {
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    double v[3] = {0, 0, 0};
+    if (a)
+        for (int c = 0; c < s->D; ++c) {
+            if (!std::isfinite(a[c])) return fail(LBM_EINVAL, "acceleration must be finite");
+            v[c] = a[c];
+        }
+    DeviceGuard dg(s->device);
+    // graphs captured the old arguments; wait for launches that use them
+    CK(cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < 3; ++c) s->acc[c] = v[c];
+    s->forced = v[0] != 0 || v[1] != 0 || v[2] != 0;
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    if (s->var >= 0 && !variant_allowed(s, s->var)) {
+        s->var = -1;  // re-tune among the kernels that implement the force
+        s->multi_k = 0;
+    }
     return LBM_OK;
 }
 

@@ -11,6 +11,13 @@
 //     the gradient (Eq. 68); u0 and rho*b go to shared memory.
 //   stage 2 (tile sites): gradient corrections, equilibrium + forcing, SRT
 //     update, store S(t+1) (site_collide).
+// Walls (a.walls, D = 2, 3): half-way bounce-back walls normal to the march
+// axis, half a site outside the lattice (Sec. III.A).  A population whose
+// source lies beyond a wall is the site's own emission in the opposite
+// direction, carrying the site's bt*; the gradient stencil sees, one plane
+// beyond a wall, the image of the plane facing it (same rho*b, reversed u0).
+// Body force (a.forced): F + rho a and G + rho (u a + a u) with the corrected
+// u = (j + F/2)/rho of Eq. 57.
 // The gradient needs rho*b on the neighbours, which exist only after the
 // neighbours have pulled; the ring is recomputed per tile and the kernel
 // marches along the slowest axis keeping three planes of (u0, rho b) in a
@@ -112,7 +119,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 
     // Stage 1 for one region site at march plane q (wrapped).  Writes u0 and
     // rho*b into aux[slot]; returns the site's values if `keep`.
-    auto stage1_site = [&](int rx, int ry, int q, int slot, bool keep, real* o_df, real* o_bt,
+    auto stage1_site = [&](int rx, int ry, int q, int slot, bool img, bool keep, real* o_df, real* o_bt,
                            real& o_rho, real* o_j, real& o_E) {
         int gx = x0 - 1 + rx;
         int gy = (D == 3) ? modp(y0 - 1 + ry, ny) : (D == 2 ? q : 0);
@@ -128,6 +135,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
             return;
         }
         if (!a.fixed_x) gx = modp(gx, nx);
+        const long long self = gx + (long long)nx * (gy + (long long)ny * gz);
         real df[Q], bsum[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
@@ -138,7 +146,13 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
             int sz = (D == 3) ? wrap1(gz - L::e(i, 2), nz) : 0;
             real v;
             real bv[NB];
-            if (a.fixed_x && (sx < 0 || sx >= nx)) {
+            const int sm = (D == 3) ? gz - L::e(i, 2) : gy - L::e(i, 1);
+            if (D > 1 && a.walls && (sm < 0 || sm >= np)) {
+                // half-way bounce-back: the site's own opposite emission
+                v = Store<FS>::ld(fin, (long long)opposite<D>(i) * N + self);
+#pragma unroll
+                for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + BLayout<D, FS>::at(k, self, N)));
+            } else if (a.fixed_x && (sx < 0 || sx >= nx)) {
                 const int side = sx < 0 ? 0 : 1;
                 const long long row = sy + (long long)ny * sz;
                 v = gf[((long long)side * Q + i) * a.rows + row];
@@ -161,7 +175,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 #pragma unroll
         for (int k = 0; k < NB; ++k) aux[(slot * NAUX + D + k) * RS + r] = rb[k];
 #pragma unroll
-        for (int c = 0; c < D; ++c) aux[(slot * NAUX + c) * RS + r] = u0[c];
+        for (int c = 0; c < D; ++c) aux[(slot * NAUX + c) * RS + r] = img ? -u0[c] : u0[c];
         if (keep) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) o_df[i] = df[i];
@@ -175,12 +189,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
     };
 
     auto stage1 = [&](int q, bool keep_next) {
-        const int qq = (D == 1) ? 0 : modp(q, np);
+        // beyond a wall: the image of the plane facing it (-1 -> 0, np -> np - 1)
+        const bool img = D > 1 && a.walls && (q < 0 || q >= np);
+        const int qq = (D == 1) ? 0 : (img ? (q < 0 ? -1 - q : 2 * np - 1 - q) : modp(q, np));
         const int slot = slot_of(q);
-        stage1_site(rxi, ryi, qq, slot, keep_next, n_df, n_bt, n_rho, n_j, n_E);
+        stage1_site(rxi, ryi, qq, slot, img, keep_next, n_df, n_bt, n_rho, n_j, n_E);
         if (tid < NRING) {
             real d_df[Q], d_bt[NB], d_rho, d_j[D], d_E;
-            stage1_site(rxr, ryr, qq, slot, false, d_df, d_bt, d_rho, d_j, d_E);
+            stage1_site(rxr, ryr, qq, slot, img, false, d_df, d_bt, d_rho, d_j, d_E);
         }
     };
 
@@ -212,6 +228,20 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
         for (int c = 0; c < D; ++c) F[c] *= real(-3);
 #pragma unroll
         for (int k = 0; k < NB; ++k) G[k] *= real(-3);
+        if (a.forced) {
+            real ga[D], ru[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                ga[c] = acc_param(a, c, real(0));
+                F[c] += c_rho * ga[c];
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) ru[c] = c_j[c] + real(0.5) * F[c];
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+#pragma unroll
+                for (int d2 = c; d2 < D; ++d2) G[sym<D>(c, d2)] += ru[c] * ga[d2] + ru[d2] * ga[c];
+        }
         site_collide<D, FS, real>(a, s, c_df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
     };
 

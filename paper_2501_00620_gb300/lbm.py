@@ -19,10 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUSY, LBM_EIO = range(8)
-LBM_BC_PERIODIC, LBM_BC_FIXED_STATE = 0, 1
+LBM_BC_PERIODIC, LBM_BC_FIXED_STATE, LBM_BC_WALLS = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
-BCS = {"periodic": LBM_BC_PERIODIC, "fixed": LBM_BC_FIXED_STATE}
+BCS = {"periodic": LBM_BC_PERIODIC, "fixed": LBM_BC_FIXED_STATE, "walls": LBM_BC_WALLS}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -113,6 +113,7 @@ def _load():
                                                      ctypes.POINTER(lbm_opts), ctypes.POINTER(vp)]
     L.lbm_init.argtypes = [vp, ctypes.POINTER(lbm_fields_in)]
     L.lbm_step.argtypes = [vp, ctypes.c_long]
+    L.lbm_set_force.argtypes = [vp, dp]
     L.lbm_sync.argtypes = [vp]
     L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
     L.lbm_diagnostics.argtypes = [vp, dp]
@@ -142,7 +143,7 @@ def _load():
     L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
-    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_sync", "lbm_moments",
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
                  "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
                  "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
@@ -194,6 +195,14 @@ def lbm_init(sim, rho, u, T):
 
 def lbm_step(sim, n):
     _check(_lib.lbm_step(sim, int(n)))
+
+
+def lbm_set_force(sim, a):
+    if a is None:
+        _check(_lib.lbm_set_force(sim, None))
+        return
+    aa = np.ascontiguousarray(a, dtype=np.float64)
+    _check(_lib.lbm_set_force(sim, _dp(aa)))
 
 
 def lbm_sync(sim):
@@ -341,6 +350,10 @@ class Simulation:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_force(self, a):
+        """Uniform body-force acceleration (dim components; None removes it)."""
+        lbm_set_force(self.h, None if a is None else np.asarray(a, dtype=np.float64)[: self.dim])
 
     def sync(self):
         lbm_sync(self.h)
