@@ -59,6 +59,9 @@ def lib():
         L.orc_nstep.argtypes = [ctypes.c_void_p]
         L.orc_nstep.restype = ctypes.c_long
         L.orc_set_force.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_model.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_model.restype = ctypes.c_int
+        L.orc_std_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
         L.orc_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
         L.orc_diagnostics.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_emitted.argtypes = [ctypes.c_void_p, dp, dp]
@@ -114,6 +117,15 @@ def beq(d, u, T):
     return out
 
 
+def std_feq(d, rho, u, T):
+    """Equilibrium of the standard-lattice comparator (Eq. 4, lattice units)."""
+    out = np.zeros(n_q(d))
+    uu = np.zeros(3)
+    uu[:d] = np.asarray(u, dtype=np.float64)[:d]
+    lib().orc_std_feq(d, float(rho), _p(uu), float(T), _p(out))
+    return out
+
+
 def forcing(d, F, G):
     out = np.zeros(n_q(d))
     FF = np.zeros(3)
@@ -137,7 +149,7 @@ class Sim:
     velocity is (d, nz, ny, nx)."""
 
     def __init__(self, d, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, thermal=False,
-                 bc="periodic"):
+                 bc="periodic", model="bump"):
         self.d, self.nx, self.ny, self.nz = d, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -147,6 +159,8 @@ class Sim:
                                    int(bool(thermal)), bcode)
         if not self._h:
             raise ValueError("oracle: invalid lattice parameters")
+        if lib().orc_set_model(self._h, {"bump": 0, "standard": 1}[model]) != 0:
+            raise ValueError("oracle: the standard comparator runs on periodic lattices")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -74,6 +74,15 @@
  *       carries both and, in a uniform flow, the work of the force goes into
  *       kinetic energy alone (the thermal T stays constant).
  *
+ * Standard-lattice comparator (model 1, periodic lattices): the textbook BGK
+ * scheme with the second-order Hermite equilibrium of Eq. 4 written in
+ * lattice units, f^eq_i = w_i rho [1 + e.u/cs2 + (u u + (T0 - cs2) I) :
+ * (e e - cs2 I) / (2 cs2^2)], collided with the same omega = 1/(tau + 1/2)
+ * and streamed like the populations of the bump scheme; no variance, no
+ * gradient correction.  Its moments through second order are rho, rho u and
+ * rho (T0 I + u u); its third moment is fixed by the lattice (Sec. I), which
+ * is what the bump scheme corrects.
+ *
  * Weights w_i = f^eq_i(rho=1, u=0), cs2 = c^2/3 = 1/3.
  */
 #include <math.h>
@@ -99,6 +108,7 @@ typedef struct {
     long N;
     double tau, T0, omega;
     int thermal, bc;           /* bc: 0 periodic, 1 fixed-state in x, 2 walls (R9) */
+    int model;                 /* 0 bump-function scheme, 1 standard comparator */
     double acc[3];             /* uniform body-force acceleration (R10) */
     long nstep;
     /* state at time t (pre-collision, post-stream) */
@@ -228,6 +238,24 @@ static void forcing(const orc_lattice *L, const double *F, const double *G, doub
                 eGe += L->e[i][a] * L->e[i][c] * G[comp_index(d, a, c)];
         }
         phi[i] = L->w[i] * (eF / cs2 + (eGe - cs2 * trG) / (2.0 * cs2 * cs2));
+    }
+}
+
+/* Standard-lattice equilibrium (Eq. 4 in lattice units, cs2 = 1/3).       */
+static void std_feq(const orc_lattice *L, double rho, const double *u, double T, double *f)
+{
+    int d = L->d;
+    double uu = 0.0;
+    for (int a = 0; a < d; ++a) uu += u[a] * u[a];
+    for (int i = 0; i < L->Q; ++i) {
+        double eu = 0.0, ee = 0.0;
+        for (int a = 0; a < d; ++a) {
+            eu += L->e[i][a] * u[a];
+            ee += (double)(L->e[i][a] * L->e[i][a]);
+        }
+        /* (u u + (T - cs2) I) : (e e - cs2 I) = (e.u)^2 - cs2 |u|^2 + (T - cs2)(|e|^2 - d cs2) */
+        double second = eu * eu - uu / 3.0 + (T - 1.0 / 3.0) * (ee - d / 3.0);
+        f[i] = L->w[i] * rho * (1.0 + 3.0 * eu + 4.5 * second);
     }
 }
 
@@ -435,6 +463,43 @@ static void phase_b(orc_sim *s)
     }
 }
 
+/* Standard comparator: moments and BGK collision with the equilibrium of
+ * Eq. 4; fs = f + omega (f^eq - f).                                        */
+static void std_moments(const orc_sim *s, long n, double *rho, double *j, double *E)
+{
+    const orc_lattice *L = &s->L;
+    const double *f = s->f + n * L->Q;
+    *rho = 0.0;
+    *E = 0.0;
+    for (int a = 0; a < 3; ++a) j[a] = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+        double ee = 0.0;
+        *rho += f[i];
+        for (int a = 0; a < L->d; ++a) {
+            j[a] += f[i] * L->e[i][a];
+            ee += (double)(L->e[i][a] * L->e[i][a]);
+        }
+        *E += f[i] * ee;
+    }
+}
+
+static void std_collide(orc_sim *s)
+{
+    const orc_lattice *L = &s->L;
+    int Q = L->Q;
+    long n;
+#pragma omp parallel for schedule(static)
+    for (n = 0; n < s->N; ++n) {
+        double rho, j[3], E, u[3] = {0.0, 0.0, 0.0}, fe[QMAX];
+        std_moments(s, n, &rho, j, &E);
+        for (int a = 0; a < L->d; ++a) u[a] = j[a] / rho;
+        std_feq(L, rho, u, s->T0, fe);
+        const double *f = s->f + n * Q;
+        double *fs = s->fs + n * Q;
+        for (int i = 0; i < Q; ++i) fs[i] = f[i] + s->omega * (fe[i] - f[i]);
+    }
+}
+
 /* Phase C: streaming of fbar (Eq. 49) and transport of bbar (Eq. 66, R4).   */
 static void phase_c(orc_sim *s)
 {
@@ -553,6 +618,11 @@ int orc_init(void *h, const double *rho, const double *u, const double *T)
         double uu[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a) uu[a] = u[a * N + n];
         if (!(rho[n] > 0) || !(T[n] > 0)) return -1;
+        if (s->model == 1) {
+            std_feq(&s->L, rho[n], uu, T[n], s->fs + n * Q);
+            for (int k = 0; k < nb; ++k) s->bs[n * nb + k] = 0.0;
+            continue;
+        }
         feq(d, rho[n], uu, s->fs + n * Q);
         beq(d, uu, T[n], s->bs + n * nb);
     }
@@ -578,14 +648,37 @@ void orc_step(void *h, long nsteps)
 {
     orc_sim *s = (orc_sim *)h;
     for (long t = 0; t < nsteps; ++t) {
-        phase_a(s);
-        phase_b(s);
+        if (s->model == 1) {
+            std_collide(s);
+        } else {
+            phase_a(s);
+            phase_b(s);
+        }
         phase_c(s);
         s->nstep++;
     }
 }
 
 long orc_nstep(void *h) { return ((orc_sim *)h)->nstep; }
+
+/* Select the scheme before orc_init: 0 bump-function (default), 1 standard
+ * comparator (periodic lattices only).  Returns 0, or -1 if not allowed.   */
+int orc_set_model(void *h, int model)
+{
+    orc_sim *s = (orc_sim *)h;
+    if (model < 0 || model > 1 || (model == 1 && s->bc != 0)) return -1;
+    s->model = model;
+    return 0;
+}
+
+void orc_std_feq(int d, double rho, const double *u, double T, double *out)
+{
+    orc_lattice L;
+    lattice_init(&L, d);
+    double uu[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) uu[a] = u[a];
+    std_feq(&L, rho, uu, T, out);
+}
 
 /* Uniform body-force acceleration (R10), d components.                    */
 void orc_set_force(void *h, const double *a)
@@ -600,8 +693,21 @@ void orc_moments(void *h, double *rho, double *u, double *T)
     orc_sim *s = (orc_sim *)h;
     int d = s->L.d;
     long N = s->N;
-    phase_a(s);
     long n;
+    if (s->model == 1) {          /* rho, u = j/rho, T = (E - rho|u|^2)/(d rho) */
+        for (n = 0; n < N; ++n) {
+            double r, j[3], E, uu = 0.0;
+            std_moments(s, n, &r, j, &E);
+            for (int a = 0; a < d; ++a) {
+                if (u) u[a * N + n] = j[a] / r;
+                uu += (j[a] / r) * (j[a] / r);
+            }
+            if (rho) rho[n] = r;
+            if (T) T[n] = (E - r * uu) / (d * r);
+        }
+        return;
+    }
+    phase_a(s);
 #pragma omp parallel for schedule(static)
     for (n = 0; n < N; ++n) {
         double F[3] = {0, 0, 0}, G[NBMAX], uu[3], Tm;
@@ -619,6 +725,20 @@ void orc_diagnostics(void *h, double *out)
     orc_sim *s = (orc_sim *)h;
     int d = s->L.d, nb = s->L.nb;
     long N = s->N;
+    if (s->model == 1) {          /* M, P = sum j, E = sum f|e|^2 */
+        double M = 0.0, P[3] = {0, 0, 0}, E = 0.0;
+        for (long n = 0; n < N; ++n) {
+            double r, j[3], e2;
+            std_moments(s, n, &r, j, &e2);
+            M += r;
+            for (int a = 0; a < d; ++a) P[a] += j[a];
+            E += e2;
+        }
+        out[0] = M;
+        for (int a = 0; a < d; ++a) out[1 + a] = P[a];
+        out[1 + d] = E;
+        return;
+    }
     double *F = malloc(sizeof(double) * 3 * N), *G = malloc(sizeof(double) * nb * N);
     phase_a(s);
     long n;
