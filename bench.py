@@ -6,7 +6,9 @@ moments, isotropic-gradient corrections, equilibrium + forcing, BGK, store,
 and the FP64 mass/momentum/energy reduction of the state (recorded every
 step).  Default workload: the 3D periodic D3Q19 256^3 solenoidal-turbulence
 configuration in FP32 (the paper's own lattice, and the largest single-GPU
-configuration); --workload tgv2d | sound1d | riemann1d select the others.
+configuration); --workload tgv2d | sound1d | riemann1d select the others,
+and --workload std3d times the standard-lattice comparator (BGK with the
+Hermite equilibrium of Eq. 4) on the same lattice as a speed reference.
 
 Prints one JSON line (rank 0).  Under torchrun each rank advances its own
 copy of the workload (independent replicas, weak scaling, no collective on
@@ -35,6 +37,8 @@ WORKLOAD_TEXT = {
               "Mach_rms 0.3; rho=1, T=T0=0.05; tau=0.52; isothermal",
     "tgv2d": "D2Q9 2048^2 periodic; Taylor-Green u0=0.1 + Gaussian rho/T pulse (amp 0.2, sigma 64); "
              "T0=0.1; tau=0.6; thermal",
+    "std3d": "standard-lattice comparator (BGK, Hermite equilibrium of Eq. 4) on D3Q19 256^3 periodic; "
+             "the turb3d velocity field (Mach 0.12 at cs2 = 1/3); T0=1/3; tau=0.52",
     "sound1d": "D1Q3 256 periodic sound wave, rho=1+1e-3 sin(2 pi x/256), T0=1/3, tau=0.8; isothermal",
     "riemann1d": "D1Q3 4096 two-state Riemann (rho 1:0.125, T 1.0:0.8 x 0.15), tau=0.55; thermal; "
                  "fixed-state ends",
@@ -157,9 +161,9 @@ def gpu_uuid(dev):
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 
-def algorithmic_bytes_per_site(d, dtype):
+def algorithmic_bytes_per_site(d, dtype, model="bump"):
     Q = {1: 3, 2: 9, 3: 19}[d]
-    NB = {1: 1, 2: 3, 3: 6}[d]
+    NB = {1: 1, 2: 3, 3: 6}[d] if model == "bump" else 0
     fb = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[dtype]
     bb = 8 if dtype == "f64" else 4
     return 2 * (Q * fb + NB * bb)   # read + write of the emitted state
@@ -201,12 +205,18 @@ def _code_only(text):
     return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
 
 
-def kernel_source_hash():
-    """Hash of the code (comments stripped) of the device sources the step
-    kernels are built from: an ncu figure taken from other code no longer
+# the comparator kernel's own sources
+KERNEL_SOURCES_BY_KERNEL = {
+    "std_step_kernel": ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_std.cu"),
+}
+
+
+def kernel_source_hash(kernel=None):
+    """Hash of the code (comments stripped) of the device sources a step
+    kernel is built from: an ncu figure taken from other code no longer
     describes the kernel."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES_BY_KERNEL.get(kernel, KERNEL_SOURCES):
         with open(os.path.join(ROOT, "paper_2501_00620_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -225,7 +235,7 @@ def profiled_traffic(kernel, workload, dtype):
         if ":" in ln and ln.strip().startswith("- "):
             k, v = ln.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != kernel_source_hash():
+    if vals.get("kernel_source_sha") != kernel_source_hash(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -260,7 +270,7 @@ def oracle_sample(name, budget_s, steps_total):
         sites_probe = c["nx"]
         n_probe = c["nx"]
     s = oracle.Sim(d, n_probe, n_probe if d >= 2 else 1, n_probe if d == 3 else 1, tau=c["tau"], T0=c["T0"],
-                   thermal=c["thermal"], bc=c["bc"])
+                   thermal=c["thermal"], bc=c["bc"], model=c.get("model", "bump"))
     s.init(rho, u, T)
     t0 = time.perf_counter()
     s.step(2)
@@ -281,7 +291,7 @@ def run_oracle(name, n, steps, warmup):
     d = c["d"]
     rho, u, T = W.fields_for(name, scale=n) if d > 1 else W.fields_for(name)
     s = oracle.Sim(d, n, n if d >= 2 else 1, n if d == 3 else 1, tau=c["tau"], T0=c["T0"],
-                   thermal=c["thermal"], bc=c["bc"])
+                   thermal=c["thermal"], bc=c["bc"], model=c.get("model", "bump"))
     s.init(rho, u, T)
     s.step(warmup)
     t0 = time.perf_counter()
@@ -501,7 +511,7 @@ def main():
     stream = torch.cuda.Stream(device=local)
     sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=c["dtype"],
                          thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True,
-                         tile=args.tile, chunk=args.chunk)
+                         tile=args.tile, chunk=args.chunk, model=c.get("model", "bump"))
     sim.init(rho, u, T)
 
     def barrier():
@@ -533,7 +543,7 @@ def main():
     ms_per_step = ms_max / args.steps
 
     # roofline of the step kernel (one launch per step)
-    bps = algorithmic_bytes_per_site(d, c["dtype"])
+    bps = algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump"))
     achieved = N * bps / (ms_per_step * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
     tile, chunk, kernel = sim.launch_config()

@@ -84,6 +84,23 @@ typedef enum {
     LBM_BF16_SHIFTED = 3  /* as above with BF16 */
 } lbm_dtype;
 
+typedef enum {
+    LBM_MODEL_BUMP = 0,     /* the bump-function scheme (Sec. II) */
+    LBM_MODEL_STANDARD = 1  /* comparator: the textbook BGK scheme with the
+                               Hermite equilibrium of Eq. 4 in lattice units,
+                               f^eq_i = w_i rho [1 + e.u/cs2 + (u u + (T0 -
+                               cs2) I) : (e e - cs2 I) / (2 cs2^2)], cs2 = 1/3,
+                               relaxed with the same omega = 1/(tau + 1/2);
+                               no variance and no gradient correction, so its
+                               shear viscosity is rho tau / 3 for any T0 (the
+                               paper's contrast, Sec. I).  Periodic lattices,
+                               no body force, ny and nz <= 65535; lbm_init's T
+                               field sets the start equilibrium, T0 the
+                               collision's; lbm_moments reports the moment
+                               temperature (E - rho|u|^2)/(d rho) and
+                               lbm_diagnostics mass, sum j, sum f|e|^2 */
+} lbm_model;
+
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc
  * returns device memory of at least `bytes` on the current device or NULL;
  * free releases it. */
@@ -115,6 +132,7 @@ typedef struct {
                                into a device history (lbm_diagnostics_history);
                                0: off */
     int use_graphs;         /* 1 (default): lbm_step replays CUDA graphs */
+    int model;              /* LBM_MODEL_BUMP (default) or LBM_MODEL_STANDARD */
 } lbm_opts;
 
 typedef struct lbm_sim lbm_sim;

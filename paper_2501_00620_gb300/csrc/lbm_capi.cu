@@ -252,7 +252,9 @@ lbm_status tma_maps(lbm_sim* s, int v, int buf, TmaArgs* ta) {
 
 // Launch variant v with arguments a; `buf` is the input buffer (a.fin).
 lbm_status launch_variant(lbm_sim* s, int v, const StepArgs& a, int buf) {
-    if (v >= kTmaBase) {
+    if (v == kStdVariant) {
+        CK(launch_std_step(s->D, s->dtype, a, s->stream));
+    } else if (v >= kTmaBase) {
         TmaArgs ta;
         lbm_status st = tma_maps(s, v, buf, &ta);
         if (st != LBM_OK) return st;
@@ -333,7 +335,7 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
 // cooperative launch on scratch copies of the state, and keeps the faster.
 lbm_status tune_multi(lbm_sim* s) {
     s->multi_k = 1;
-    if (s->D != 1 || s->opts.steps_per_launch == 1) return LBM_OK;
+    if (s->D != 1 || s->opts.steps_per_launch == 1 || s->opts.model == LBM_MODEL_STANDARD) return LBM_OK;
     if (s->opts.steps_per_launch > 1) {  // forced
         s->multi_k = s->opts.steps_per_launch;
         return LBM_OK;
@@ -421,6 +423,11 @@ lbm_status tune_multi(lbm_sim* s) {
 }
 
 lbm_status autotune(lbm_sim* s) {
+    if (s->opts.model == LBM_MODEL_STANDARD) {  // one kernel, planes per block fixed
+        s->var = kStdVariant;
+        s->chunk = s->opts.chunk > 0 ? s->opts.chunk : 32;
+        return ensure_partial(s, s->var, s->chunk);
+    }
     auto key = std::make_tuple(s->D, s->dtype * 2 + (generic_only(s) ? 1 : 0), s->nx, s->ny, s->nz);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -585,6 +592,9 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
         lbm_default_opts(&o);
     if (o.dtype < LBM_F64 || o.dtype > LBM_BF16_SHIFTED) return fail(LBM_EINVAL, "unknown dtype");
     if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(LBM_EINVAL, "alloc and free go together");
+    if (o.model != LBM_MODEL_BUMP && o.model != LBM_MODEL_STANDARD) return fail(LBM_EINVAL, "unknown model");
+    if (o.model == LBM_MODEL_STANDARD && (bc != LBM_BC_PERIODIC || ny > 65535 || nz > 65535))
+        return fail(LBM_EINVAL, "the standard comparator runs on periodic lattices with ny, nz <= 65535");
     long long N = (long long)nx * ny * nz;
     int Q = q_of(dim), NB = nb_of(dim);
     if ((long long)Q * N >= (1LL << 40)) return fail(LBM_EINVAL, "lattice too large");
@@ -685,7 +695,13 @@ lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
     CK(cudaMemcpyAsync(u, in->u, (size_t)s->D * N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(T, in->T, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     s->cur = 0;
-    CK(launch_init(s->D, s->dtype, rho, u, T, s->f[0], s->b[0], N, s->stream));
+    if (s->opts.model == LBM_MODEL_STANDARD) {
+        CK(launch_std_init(s->D, s->dtype, rho, u, T, s->f[0], N, s->stream));
+        for (int k = 0; k < 2; ++k)  // no variance: keep both buffers defined
+            CK(cudaMemsetAsync(s->b[k], 0, (size_t)s->NB * N * rbytes_of(s->dtype), s->stream));
+    } else {
+        CK(launch_init(s->D, s->dtype, rho, u, T, s->f[0], s->b[0], N, s->stream));
+    }
     if (s->bc == LBM_BC_FIXED_STATE)
         CK(launch_reservoir(s->D, s->dtype, rho, u, T, s->nx, s->rows, N, s->gf, s->gb, s->gaux, s->stream));
     CK(cudaMemsetAsync(s->step_ctr, 0, 64, s->stream));
@@ -698,6 +714,7 @@ lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
 
 lbm_status lbm_set_force(lbm_sim* s, const double* a) {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (s->opts.model == LBM_MODEL_STANDARD && a) return fail(LBM_EINVAL, "the standard comparator has no body force");
     double v[3] = {0, 0, 0};
     if (a)
         for (int c = 0; c < s->D; ++c) {

@@ -41,6 +41,7 @@ int device_sms() {
 int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_variants_d3(), 0); }
 
 const char* kernel_name(int D, int v) {
+    if (v == kStdVariant) return "std_step_kernel";
     if (v >= kTmaBase) return "step_fast_kernel";
     return (D == 2 && v == 3) ? "step_strip_kernel" : "step_kernel";
 }
@@ -75,6 +76,7 @@ cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStre
 }
 
 dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk) {
+    if (v == kStdVariant) return std_grid(D, nx, ny, nz, chunk);
     Variant t = v >= 0 ? variant(D, v) : Variant{1, 1};
     dim3 g(1, 1, 1);
     g.x = (nx + t.tx - 1) / t.tx;

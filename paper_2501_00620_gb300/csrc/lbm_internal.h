@@ -23,6 +23,9 @@ constexpr int kStripNT = 256;
 // kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;
 
+// Variant index of the standard-lattice comparator kernel (lbm_std.cu).
+constexpr int kStdVariant = 1000;
+
 // Slice geometry of a TMA variant (for the host-side tensor maps).
 struct TmaBox {
     int sxf, sxb, sy, pxf, smem;
@@ -57,5 +60,12 @@ cudaError_t launch_get_state(int D, int dtype, const void* f, const void* b, dou
                              long long N, cudaStream_t st);
 cudaError_t launch_set_state(int D, int dtype, void* f, void* b, const double* fi, const double* bi,
                              long long N, cudaStream_t st);
+
+// Standard-lattice comparator (lbm_std.cu): grid of a step launch, one step,
+// and the start (equilibrium of Eq. 4 for the fields, populations only).
+dim3 std_grid(int D, int nx, int ny, int nz, int chunk);
+cudaError_t launch_std_step(int D, int dtype, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_std_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
+                            long long N, cudaStream_t st);
 
 }  // namespace lbm

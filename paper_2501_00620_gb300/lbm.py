@@ -23,6 +23,8 @@ LBM_BC_PERIODIC, LBM_BC_FIXED_STATE, LBM_BC_WALLS = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
 BCS = {"periodic": LBM_BC_PERIODIC, "fixed": LBM_BC_FIXED_STATE, "walls": LBM_BC_WALLS}
+LBM_MODEL_BUMP, LBM_MODEL_STANDARD = 0, 1
+MODELS = {"bump": LBM_MODEL_BUMP, "standard": LBM_MODEL_STANDARD}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -42,6 +44,7 @@ class lbm_opts(ctypes.Structure):
         ("steps_per_launch", ctypes.c_int),
         ("diagnostics", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
+        ("model", ctypes.c_int),
     ]
 
 
@@ -308,7 +311,7 @@ class Simulation:
 
     def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
                  thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
-                 use_graphs=True, torch_allocator=False, steps_per_launch=0):
+                 use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump"):
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -323,6 +326,7 @@ class Simulation:
         o.diagnostics = int(bool(diagnostics))
         o.use_graphs = int(bool(use_graphs))
         o.steps_per_launch = int(steps_per_launch)
+        o.model = MODELS[model] if isinstance(model, str) else int(model)
         self._allocator = None
         if torch_allocator:
             self._allocator = TorchAllocator(device)

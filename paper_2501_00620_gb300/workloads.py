@@ -114,6 +114,11 @@ CONFIGS = {
                   bc="periodic", steps=10000, dtype="f32"),
     "turb3d": dict(d=3, nx=256, ny=256, nz=256, tau=0.52, T0=0.05, thermal=False,
                    bc="periodic", steps=2000, dtype="f32"),
+    # the standard-lattice comparator on the turb3d velocity field, at its
+    # native temperature cs2 = 1/3 (at T0 = 0.05 its diagonal equilibria
+    # would be negative)
+    "std3d": dict(d=3, nx=256, ny=256, nz=256, tau=0.52, T0=1.0 / 3.0, thermal=False,
+                  bc="periodic", steps=2000, dtype="f32", model="standard"),
 }
 
 
@@ -130,6 +135,11 @@ def fields_for(name, scale=None, seed=0):
     if name == "turb3d":
         n = scale or c["nx"]
         return solenoidal_3d(n, k0=8.0 * n / 256.0, T0=c["T0"], thermal=c["thermal"], seed=seed)
+    if name == "std3d":
+        n = scale or c["nx"]
+        t = CONFIGS["turb3d"]
+        rho, u, _ = solenoidal_3d(n, k0=8.0 * n / 256.0, T0=t["T0"], thermal=False, seed=seed)
+        return rho, u, np.full_like(rho, c["T0"])
     raise KeyError(name)
 
 

@@ -30,7 +30,7 @@ def take_window(a, idx):
     return a[:, iz][:, :, iy][:, :, :, ix]
 
 
-def check_windows(d, f0, b0, f1, b1, tau, T0, thermal, n_windows=6, half=5, seed=0):
+def check_windows(d, f0, b0, f1, b1, tau, T0, thermal, n_windows=6, half=5, seed=0, model="bump"):
     """f0/b0: emitted state at t (full lattice, FP64 planes); f1/b1: the GPU's
     emitted state at t+1.  For random windows, restart the oracle from the
     window of (f0, b0), take one step and compare the window interior (sites
@@ -44,7 +44,7 @@ def check_windows(d, f0, b0, f1, b1, tau, T0, thermal, n_windows=6, half=5, seed
         idx = window_indices(shape, center, half)
         wf, wb = take_window(f0, idx), take_window(b0, idx)
         wz, wy, wx = wf.shape[1:]
-        s = oracle.Sim(d, wx, wy, wz, tau=tau, T0=T0, thermal=thermal)
+        s = oracle.Sim(d, wx, wy, wz, tau=tau, T0=T0, thermal=thermal, model=model)
         s.set_emitted(wf, wb)
         s.step(1)
         of, ob = s.emitted()
