@@ -60,6 +60,8 @@ def lib():
         L.orc_nstep.restype = ctypes.c_long
         L.orc_set_force.argtypes = [ctypes.c_void_p, dp]
         L.orc_set_model.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_wall_velocity.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_set_wall_velocity.restype = ctypes.c_int
         L.orc_set_model.restype = ctypes.c_int
         L.orc_std_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
         L.orc_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
@@ -160,7 +162,7 @@ class Sim:
         if not self._h:
             raise ValueError("oracle: invalid lattice parameters")
         if lib().orc_set_model(self._h, {"bump": 0, "standard": 1}[model]) != 0:
-            raise ValueError("oracle: the standard comparator runs on periodic lattices")
+            raise ValueError("oracle: the standard comparator runs on periodic or walled lattices")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -177,6 +179,14 @@ class Sim:
 
     def step(self, n=1):
         lib().orc_step(self._h, int(n))
+
+    def set_wall_velocity(self, lo, hi):
+        """Tangential velocities of the lower and upper walls (d components)."""
+        ll, hh = np.zeros(3), np.zeros(3)
+        ll[:self.d] = np.asarray(lo, dtype=np.float64)[:self.d]
+        hh[:self.d] = np.asarray(hi, dtype=np.float64)[:self.d]
+        if lib().orc_set_wall_velocity(self._h, _p(ll), _p(hh)) != 0:
+            raise ValueError("oracle: wall velocities need walls and must be tangential")
 
     def set_force(self, a):
         """Uniform body-force acceleration (d components)."""

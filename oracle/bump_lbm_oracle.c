@@ -66,6 +66,15 @@
  *       gradient stencil sees, one site beyond a wall, the image of the fluid
  *       site facing it across the wall: the same rho*b and the reversed u0
  *       (bounce-back reverses velocities and leaves the variance unchanged).
+ *   R12 Moving walls (Sec. III.D's Couette flow): a wall may move along
+ *       itself with velocity u_w (lower wall u_lo, upper wall u_hi).  A
+ *       population bounced at it gains the momentum of the wall,
+ *       fbar_i(x, t+1) = fbar*_-i(x, t) + 6 w_i rho(x, t) e_i.u_w, with
+ *       rho(x, t) the sum of the site's own emissions (the odd part of the
+ *       equilibrium is exactly 6 w_i rho e_i.u, so a site moving with the
+ *       wall at equilibrium is reproduced); its bbar is unchanged.  The
+ *       gradient stencil's image velocity is reflected about the wall's,
+ *       2 u_w - u0.
  *   R10 Body force (Sec. III.A drives Poiseuille flow by a uniform
  *       acceleration a): the force density rho a joins the gradient force,
  *       F -> F + rho a, and its second-moment source joins G,
@@ -74,12 +83,13 @@
  *       carries both and, in a uniform flow, the work of the force goes into
  *       kinetic energy alone (the thermal T stays constant).
  *
- * Standard-lattice comparator (model 1, periodic lattices): the textbook BGK
+ * Standard-lattice comparator (model 1; periodic, or walls): the textbook BGK
  * scheme with the second-order Hermite equilibrium of Eq. 4 written in
  * lattice units, f^eq_i = w_i rho [1 + e.u/cs2 + (u u + (T0 - cs2) I) :
  * (e e - cs2 I) / (2 cs2^2)], collided with the same omega = 1/(tau + 1/2)
  * and streamed like the populations of the bump scheme; no variance, no
- * gradient correction.  Its moments through second order are rho, rho u and
+ * gradient correction.  A body force enters by the textbook second-order
+ * forcing (the projection R5 with F = rho a, G = rho (u a + a u)).  Its moments through second order are rho, rho u and
  * rho (T0 I + u u); its third moment is fixed by the lattice (Sec. I), which
  * is what the bump scheme corrects.
  *
@@ -110,6 +120,7 @@ typedef struct {
     int thermal, bc;           /* bc: 0 periodic, 1 fixed-state in x, 2 walls (R9) */
     int model;                 /* 0 bump-function scheme, 1 standard comparator */
     double acc[3];             /* uniform body-force acceleration (R10) */
+    double uw[2][3];           /* wall velocities (R12): [0] lower, [1] upper */
     long nstep;
     /* state at time t (pre-collision, post-stream) */
     double *f, *b;
@@ -305,20 +316,23 @@ static int wall_coord(const orc_sim *s, int y, int z) { return s->L.d == 3 ? z :
 static int wall_extent(const orc_sim *s) { return s->L.d == 3 ? s->nz : s->ny; }
 
 /* Gradient-stencil neighbour (x,y,z) + e under the walls of R9: the fluid
- * site facing it across the wall, with *sign = -1 for the reversed u0.      */
-static long grad_neighbour(const orc_sim *s, int x, int y, int z, const int *e, double *sign)
+ * site facing it across the wall.  *wall = -1 for a fluid neighbour, else
+ * the wall crossed (0 lower, 1 upper), whose image velocity is
+ * 2 u_w - u0 (R9, R12).                                                    */
+static long grad_neighbour(const orc_sim *s, int x, int y, int z, const int *e, int *wall)
 {
-    *sign = 1.0;
+    *wall = -1;
     if (s->bc != 2) return neighbour(s, x, y, z, e[0], e[1], e[2]);
     int X = x + e[0], Y = y + e[1], Z = z + e[2];
     int w = wall_coord(s, Y, Z), n = wall_extent(s);
     if (w < 0 || w >= n) {
         int m = w < 0 ? -1 - w : 2 * n - 1 - w;      /* mirror across the wall */
         if (s->L.d == 3) Z = m; else Y = m;
-        *sign = -1.0;
+        *wall = w < 0 ? 0 : 1;
     }
     return neighbour(s, X, Y, Z, 0, 0, 0);
 }
+
 
 static void site_coords(const orc_sim *s, long n, int *x, int *y, int *z)
 {
@@ -332,6 +346,13 @@ static const double *fs_at(const orc_sim *s, long k) { return k >= 0 ? s->fs + k
 static const double *bs_at(const orc_sim *s, long k) { return k >= 0 ? s->bs + k * s->L.nb : s->g_bs + (-1 - k) * s->L.nb; }
 static const double *u0_at(const orc_sim *s, long k) { return k >= 0 ? s->u0 + k * 3 : s->g_u + (-1 - k) * 3; }
 static const double *rb_at(const orc_sim *s, long k) { return k >= 0 ? s->rb + k * s->L.nb : s->g_rb + (-1 - k) * s->L.nb; }
+
+/* u0 seen by the gradient stencil at neighbour m across `wall` (or not).   */
+static void image_u0(const orc_sim *s, long m, int wall, double *u)
+{
+    const double *u0 = u0_at(s, m);
+    for (int a = 0; a < 3; ++a) u[a] = wall < 0 ? u0[a] : 2.0 * s->uw[wall][a] - u0[a];
+}
 
 /* ---------------------------------------------------------------------- */
 /* Phase A: uncorrected moments and rho*b for the gradient (Eqs. 56-57, 68) */
@@ -377,8 +398,8 @@ static double grad_rb(const orc_sim *s, int x, int y, int z, int a, int k)
     double acc = 0.0;
     for (int i = 1; i < L->Q; ++i) {
         if (L->e[i][a] == 0) continue;
-        double sg;
-        long m = grad_neighbour(s, x, y, z, L->e[i], &sg);
+        int wall;
+        long m = grad_neighbour(s, x, y, z, L->e[i], &wall);
         acc += L->w[i] * L->e[i][a] * rb_at(s, m)[k];
     }
     return 3.0 * acc;
@@ -391,10 +412,12 @@ static double grad_H(const orc_sim *s, int x, int y, int z, int a, int bb, int c
     double acc = 0.0;
     for (int i = 1; i < L->Q; ++i) {
         if (L->e[i][a] == 0) continue;
-        double sg;
-        long m = grad_neighbour(s, x, y, z, L->e[i], &sg);
-        const double *u = u0_at(s, m), *r = rb_at(s, m);
-        double H = sg * (u[c] * r[comp_index(d, a, bb)] + u[bb] * r[comp_index(d, c, a)]);
+        int wall;
+        double u[3];
+        long m = grad_neighbour(s, x, y, z, L->e[i], &wall);
+        image_u0(s, m, wall, u);
+        const double *r = rb_at(s, m);
+        double H = u[c] * r[comp_index(d, a, bb)] + u[bb] * r[comp_index(d, c, a)];
         acc += L->w[i] * L->e[i][a] * H;
     }
     return 3.0 * acc;
@@ -486,17 +509,28 @@ static void std_moments(const orc_sim *s, long n, double *rho, double *j, double
 static void std_collide(orc_sim *s)
 {
     const orc_lattice *L = &s->L;
-    int Q = L->Q;
+    int Q = L->Q, d = L->d;
     long n;
 #pragma omp parallel for schedule(static)
     for (n = 0; n < s->N; ++n) {
         double rho, j[3], E, u[3] = {0.0, 0.0, 0.0}, fe[QMAX];
+        double F[3] = {0.0, 0.0, 0.0}, G[NBMAX], phi[QMAX];
         std_moments(s, n, &rho, j, &E);
-        for (int a = 0; a < L->d; ++a) u[a] = j[a] / rho;
+        /* body force: the textbook second-order (Guo-type) scheme, i.e. the
+         * forcing projection R5 with F = rho a, G = rho (u a + a u) and the
+         * half-force velocity, weighted by omega tau = 1 - omega/2 */
+        for (int a = 0; a < d; ++a) {
+            F[a] = rho * s->acc[a];
+            u[a] = (j[a] + 0.5 * F[a]) / rho;
+        }
+        for (int a = 0; a < d; ++a)
+            for (int c = a; c < d; ++c)
+                G[comp_index(d, a, c)] = rho * (u[a] * s->acc[c] + u[c] * s->acc[a]);
         std_feq(L, rho, u, s->T0, fe);
+        forcing(L, F, G, phi);
         const double *f = s->f + n * Q;
         double *fs = s->fs + n * Q;
-        for (int i = 0; i < Q; ++i) fs[i] = f[i] + s->omega * (fe[i] - f[i]);
+        for (int i = 0; i < Q; ++i) fs[i] = f[i] + s->omega * (fe[i] - f[i]) + s->omega * s->tau * phi[i];
     }
 }
 
@@ -517,8 +551,14 @@ static void phase_c(orc_sim *s)
             const double *bm;
             int w = wall_coord(s, y - L->e[i][1], z - L->e[i][2]);
             if (s->bc == 2 && (w < 0 || w >= wall_extent(s))) {
-                /* half-way bounce-back (R9): the site's own opposite emission */
-                fi = s->fs[n * Q + L->opp[i]];
+                /* half-way bounce-back (R9): the site's own opposite
+                 * emission, plus the wall's momentum (R12) */
+                const double *uw = s->uw[w < 0 ? 0 : 1];
+                double eu = 0.0, rho0 = 0.0;
+                for (int a = 0; a < L->d; ++a) eu += L->e[i][a] * uw[a];
+                if (eu != 0.0)
+                    for (int k = 0; k < Q; ++k) rho0 += s->fs[n * Q + k];
+                fi = s->fs[n * Q + L->opp[i]] + 6.0 * L->w[i] * rho0 * eu;
                 bm = s->bs + n * nb;
             } else {
                 long m = neighbour(s, x, y, z, -L->e[i][0], -L->e[i][1], -L->e[i][2]);
@@ -662,11 +702,12 @@ void orc_step(void *h, long nsteps)
 long orc_nstep(void *h) { return ((orc_sim *)h)->nstep; }
 
 /* Select the scheme before orc_init: 0 bump-function (default), 1 standard
- * comparator (periodic lattices only).  Returns 0, or -1 if not allowed.   */
+ * comparator (periodic lattices or the walls of R9/R12, which bounce its
+ * populations the same way).  Returns 0, or -1 if not allowed.            */
 int orc_set_model(void *h, int model)
 {
     orc_sim *s = (orc_sim *)h;
-    if (model < 0 || model > 1 || (model == 1 && s->bc != 0)) return -1;
+    if (model < 0 || model > 1 || (model == 1 && s->bc == 1)) return -1;
     s->model = model;
     return 0;
 }
@@ -678,6 +719,20 @@ void orc_std_feq(int d, double rho, const double *u, double T, double *out)
     double uu[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) uu[a] = u[a];
     std_feq(&L, rho, uu, T, out);
+}
+
+/* Wall velocities (R12): lower and upper, d components each, tangential
+ * (the wall-normal component must be 0).  Returns 0, or -1 if not allowed. */
+int orc_set_wall_velocity(void *h, const double *lo, const double *hi)
+{
+    orc_sim *s = (orc_sim *)h;
+    int d = s->L.d, an = d - 1;
+    if (s->bc != 2 || lo[an] != 0.0 || hi[an] != 0.0) return -1;
+    for (int a = 0; a < 3; ++a) {
+        s->uw[0][a] = a < d ? lo[a] : 0.0;
+        s->uw[1][a] = a < d ? hi[a] : 0.0;
+    }
+    return 0;
 }
 
 /* Uniform body-force acceleration (R10), d components.                    */
@@ -694,13 +749,14 @@ void orc_moments(void *h, double *rho, double *u, double *T)
     int d = s->L.d;
     long N = s->N;
     long n;
-    if (s->model == 1) {          /* rho, u = j/rho, T = (E - rho|u|^2)/(d rho) */
+    if (s->model == 1) {          /* rho, u = (j + rho a/2)/rho, T = (E - rho|u|^2)/(d rho) */
         for (n = 0; n < N; ++n) {
             double r, j[3], E, uu = 0.0;
             std_moments(s, n, &r, j, &E);
             for (int a = 0; a < d; ++a) {
-                if (u) u[a * N + n] = j[a] / r;
-                uu += (j[a] / r) * (j[a] / r);
+                double ua = (j[a] + 0.5 * r * s->acc[a]) / r;
+                if (u) u[a * N + n] = ua;
+                uu += ua * ua;
             }
             if (rho) rho[n] = r;
             if (T) T[n] = (E - r * uu) / (d * r);
@@ -731,7 +787,7 @@ void orc_diagnostics(void *h, double *out)
             double r, j[3], e2;
             std_moments(s, n, &r, j, &e2);
             M += r;
-            for (int a = 0; a < d; ++a) P[a] += j[a];
+            for (int a = 0; a < d; ++a) P[a] += j[a] + 0.5 * r * s->acc[a];
             E += e2;
         }
         out[0] = M;

@@ -17,7 +17,13 @@ site outside the lattice, so z is measured from -1/2.
 * D2Q9 (walls normal to y) and D3Q19 (walls normal to z, uniform in x, y)
   give the same profile, which ties the two wall paths together;
 * hydrostatics with the force normal to the walls: T d(rho)/dz = rho a_z
-  (the z-equation of the Couette problem of Sec. III.D), rho ~ exp(a z / T).
+  (the z-equation of the Couette problem of Sec. III.D), rho ~ exp(a z / T);
+* moving walls (Sec. III.D): plane Couette flow is the exact linear profile;
+  with gravity normal to the walls the profile follows the closed form
+  u = u_b + (u_t - u_b) (1 - exp(-a z / T)) / (1 - exp(-a H / T)), and the
+  frame shift (0, U) -> (-U/2, U/2) moves the profile by -U/2 only;
+* the standard-lattice comparator in the same channel has eta = rho tau / 3
+  whatever T is (Sec. I) -- the contrast to eta = rho T tau above.
 
 A planted mistake in the wall image of the gradient stencil (u0 not reversed)
 moves eta / (rho T tau) at T = 0.1 by about 9%, far outside these bounds.
@@ -28,9 +34,9 @@ import pytest
 import oracle
 
 
-def poiseuille(d, H, tau, T, a=1e-6, steps=None):
+def poiseuille(d, H, tau, T, a=1e-6, steps=None, model="bump"):
     if d == 2:
-        s = oracle.Sim(2, 1, H, tau=tau, T0=T, bc="walls")
+        s = oracle.Sim(2, 1, H, tau=tau, T0=T, bc="walls", model=model)
         shape = (1, H, 1)
     else:
         s = oracle.Sim(3, 1, 1, H, tau=tau, T0=T, bc="walls")
@@ -150,3 +156,59 @@ def test_hydrostatic_profile():
     slope = np.polyfit(z[2:-2], np.log(rho[2:-2]), 1)[0]
     assert abs(slope / (a / T) - 1) < 2e-2
     assert np.abs(u).max() < 1e-3 * abs(a) * H
+
+
+def couette(d, H, tau, T, ub, ut, g, steps=None):
+    """Walls moving along x (2D) / y (3D) at ub (lower) and ut (upper),
+    gravity g along the wall normal; returns rho and the wall-parallel u."""
+    if d == 2:
+        s = oracle.Sim(2, 1, H, tau=tau, T0=T, bc="walls")
+        s.init(1.0, np.zeros((2, 1, H, 1)), T)
+        s.set_wall_velocity([ub, 0.0], [ut, 0.0])
+        s.set_force([0.0, g])
+    else:
+        s = oracle.Sim(3, 1, 1, H, tau=tau, T0=T, bc="walls")
+        s.init(1.0, np.zeros((3, H, 1, 1)), T)
+        s.set_wall_velocity([0.0, ub, 0.0], [0.0, ut, 0.0])
+        s.set_force([0.0, 0.0, g])
+    s.step(steps if steps is not None else int(8 * H * H / (T * tau)))
+    rho, u, _ = s.moments()
+    return rho.ravel(), (u[0] if d == 2 else u[1]).ravel()
+
+
+def test_couette_linear_exact():
+    H, U = 32, 0.02
+    _, u = couette(2, H, 0.6, 0.1, 0.0, U, 0.0)
+    z = np.arange(H) + 0.5
+    assert np.abs(u - U * z / H).max() < 1e-10 * U
+
+
+def test_couette_gravity_closed_form_and_frame_shift():
+    """Sec. III.D: T = 0.1, a_z = -1e-3 (density ratio 1.35 across the
+    channel).  Profile within 1.5% of U of the closed form; the shifted frame
+    within 1% of U of the shifted profile."""
+    H, U, T, g = 32, 0.02, 0.1, -1e-3
+    z = np.arange(H) + 0.5
+    _, ua = couette(2, H, 0.6, T, 0.0, U, g)
+    _, ub = couette(2, H, 0.6, T, -U / 2, U / 2, g)
+    k = g / T
+    exact = U * (1 - np.exp(-k * z)) / (1 - np.exp(-k * H))
+    assert np.abs(ua - exact).max() < 1.5e-2 * U
+    assert np.abs(ub + U / 2 - ua).max() < 1e-2 * U
+
+
+def test_couette_3d_equals_2d():
+    r2, u2 = couette(2, 12, 0.6, 0.15, -0.01, 0.02, -1e-3, steps=600)
+    r3, u3 = couette(3, 12, 0.6, 0.15, -0.01, 0.02, -1e-3, steps=600)
+    assert np.abs(r2 - r3).max() < 1e-13
+    assert np.abs(u2 - u3).max() < 1e-13
+
+
+@pytest.mark.parametrize("T", [0.2, 1 / 3])
+def test_standard_poiseuille_viscosity_ignores_T(T):
+    """The comparator (textbook BGK, Eq. 4) in the same channel: eta = rho tau / 3
+    at T0 = 0.2 and 1/3, against the bump scheme's rho T tau."""
+    H, a, tau = 32, 1e-6, 0.5
+    rho, ux, _ = poiseuille(2, H, tau, T, a, steps=int(6 * H * H / (tau / 3)), model="standard")
+    eta = rho.mean() * a * H * H / (8 * ux.max())
+    assert abs(eta / (rho.mean() * tau / 3) - 1) < 1.5e-2
