@@ -173,6 +173,19 @@ lbm_status lbm_init(lbm_sim *sim, const lbm_fields_in *fields);
  * simulation's stream.  LBM_EINVAL for a NULL sim or a non-finite value. */
 lbm_status lbm_set_force(lbm_sim *sim, const double *a);
 
+/* Velocities of the walls of an LBM_BC_WALLS lattice (Sec. III.D's Couette
+ * flow): `lo` and `hi` point at dim host doubles each, the velocity of the
+ * lower and upper wall (copied; NULL means at rest).  Walls move along
+ * themselves: the component along the last axis must be 0.  A population
+ * bounced at a moving wall gains 6 w_i rho e_i.u_w, rho the density of the
+ * site at t (the odd part of the equilibrium), and the gradient stencil's
+ * image velocity is 2 u_w - u0.  Takes effect at the next streaming: the
+ * start state of lbm_init is an emission that the first lbm_step streams,
+ * so velocities set before that step apply to it.  Waits for the
+ * simulation's stream.  LBM_EINVAL without walls, for a normal component
+ * or a non-finite value. */
+lbm_status lbm_set_wall_velocity(lbm_sim *sim, const double *lo, const double *hi);
+
 /* Advance n >= 0 time steps (Sec. II.C, Eqs. 49-68): asynchronous on the
  * simulation's stream. */
 lbm_status lbm_step(lbm_sim *sim, long n);

@@ -33,11 +33,17 @@ struct StepArgs {
     int forced;           // 1: uniform body force of acceleration acc
     double acc[3];        // body-force acceleration (lattice units)
     float acc_f[3];       // the same, rounded to FP32 on the host
+    int walls_moving;     // 1: a wall has a nonzero (tangential) velocity
+    double uw[2][3];      // wall velocities: [0] lower, [1] upper wall
+    float uw_f[2][3];
 };
 
 // Body-force acceleration in the arithmetic type R.
 __host__ __device__ __forceinline__ double acc_param(const StepArgs& a, int c, double) { return a.acc[c]; }
 __host__ __device__ __forceinline__ float acc_param(const StepArgs& a, int c, float) { return a.acc_f[c]; }
+// Wall velocity (side 0 lower, 1 upper) in the arithmetic type R.
+__host__ __device__ __forceinline__ double uw_param(const StepArgs& a, int side, int c, double) { return a.uw[side][c]; }
+__host__ __device__ __forceinline__ float uw_param(const StepArgs& a, int side, int c, float) { return a.uw_f[side][c]; }
 
 // omega, tau, T0 in the arithmetic type R (no per-site conversion from FP64).
 __host__ __device__ __forceinline__ void step_params(const StepArgs& a, double& omega, double& tau, double& T0) {

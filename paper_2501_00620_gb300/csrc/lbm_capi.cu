@@ -66,6 +66,8 @@ struct lbm_sim {
     int bc = 0;
     double acc[3] = {0, 0, 0};  // body-force acceleration
     bool forced = false;
+    double uw[2][3] = {{0, 0, 0}, {0, 0, 0}};  // wall velocities (lower, upper)
+    bool walls_moving = false;
     lbm_opts opts{};
     int dtype = 0;
     int device = 0;
@@ -143,6 +145,12 @@ StepArgs base_args(const lbm_sim* s) {
         a.acc[c] = s->acc[c];
         a.acc_f[c] = (float)s->acc[c];
     }
+    a.walls_moving = s->walls_moving ? 1 : 0;
+    for (int w = 0; w < 2; ++w)
+        for (int c = 0; c < 3; ++c) {
+            a.uw[w][c] = s->uw[w][c];
+            a.uw_f[w][c] = (float)s->uw[w][c];
+        }
     a.rows = s->rows;
     a.gf = s->gf;
     a.gb = s->gb;
@@ -735,6 +743,36 @@ lbm_status lbm_set_force(lbm_sim* s, const double* a) {
         s->var = -1;  // re-tune among the kernels that implement the force
         s->multi_k = 0;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_sim* s, const double* lo, const double* hi) {
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (s->bc != LBM_BC_WALLS) return fail(LBM_EINVAL, "wall velocities need LBM_BC_WALLS");
+    double v[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    const double* in[2] = {lo, hi};
+    for (int w = 0; w < 2; ++w)
+        if (in[w])
+            for (int c = 0; c < s->D; ++c) {
+                if (!std::isfinite(in[w][c])) return fail(LBM_EINVAL, "wall velocity must be finite");
+                v[w][c] = in[w][c];
+            }
+    if (v[0][s->D - 1] != 0 || v[1][s->D - 1] != 0)
+        return fail(LBM_EINVAL, "wall velocities must be tangential (zero along the last axis)");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));  // graphs captured the old arguments
+    bool moving = false;
+    for (int w = 0; w < 2; ++w)
+        for (int c = 0; c < 3; ++c) {
+            s->uw[w][c] = v[w][c];
+            moving = moving || v[w][c] != 0;
+        }
+    s->walls_moving = moving;
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
     return LBM_OK;
 }
 

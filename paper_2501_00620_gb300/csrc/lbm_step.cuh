@@ -16,6 +16,10 @@
 // source lies beyond a wall is the site's own emission in the opposite
 // direction, carrying the site's bt*; the gradient stencil sees, one plane
 // beyond a wall, the image of the plane facing it (same rho*b, reversed u0).
+// A moving wall (a.walls_moving, velocity u_w along the wall) adds its
+// momentum to a bounced population, 6 w_i rho(x, t) e_i.u_w with rho(x, t)
+// the sum of the site's own emissions, and the image velocity is reflected
+// about the wall's, 2 u_w - u0 (Sec. III.D).
 // Body force (a.forced): F + rho a and G + rho (u a + a u) with the corrected
 // u = (j + F/2)/rho of Eq. 57.
 // The gradient needs rho*b on the neighbours, which exist only after the
@@ -119,7 +123,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 
     // Stage 1 for one region site at march plane q (wrapped).  Writes u0 and
     // rho*b into aux[slot]; returns the site's values if `keep`.
-    auto stage1_site = [&](int rx, int ry, int q, int slot, bool img, bool keep, real* o_df, real* o_bt,
+    auto stage1_site = [&](int rx, int ry, int q, int slot, int img, bool keep, real* o_df, real* o_bt,
                            real& o_rho, real* o_j, real& o_E) {
         int gx = x0 - 1 + rx;
         int gy = (D == 3) ? modp(y0 - 1 + ry, ny) : (D == 2 ? q : 0);
@@ -136,6 +140,16 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
         }
         if (!a.fixed_x) gx = modp(gx, nx);
         const long long self = gx + (long long)nx * (gy + (long long)ny * gz);
+        // density of this site at t (sum of its emissions) for the momentum a
+        // moving wall gives to the populations bounced there
+        real rho_self = real(1);
+        if (D > 1 && a.walls_moving) {
+            const int gw = (D == 3) ? gz : gy;
+            if (gw == 0 || gw == np - 1) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) rho_self += Store<FS>::ld(fin, (long long)k * N + self);
+            }
+        }
         real df[Q], bsum[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
@@ -148,8 +162,17 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
             real bv[NB];
             const int sm = (D == 3) ? gz - L::e(i, 2) : gy - L::e(i, 1);
             if (D > 1 && a.walls && (sm < 0 || sm >= np)) {
-                // half-way bounce-back: the site's own opposite emission
+                // half-way bounce-back: the site's own opposite emission,
+                // plus the momentum of a moving wall
                 v = Store<FS>::ld(fin, (long long)opposite<D>(i) * N + self);
+                if (a.walls_moving) {
+                    const int side = sm < 0 ? 0 : 1;
+                    real eu = real(0);
+#pragma unroll
+                    for (int c = 0; c < D; ++c)
+                        if (L::e(i, c) != 0) eu += real(L::e(i, c)) * uw_param(a, side, c, real(0));
+                    v += real(6) * real(L::w(i)) * rho_self * eu;
+                }
 #pragma unroll
                 for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + BLayout<D, FS>::at(k, self, N)));
             } else if (a.fixed_x && (sx < 0 || sx >= nx)) {
@@ -175,7 +198,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 #pragma unroll
         for (int k = 0; k < NB; ++k) aux[(slot * NAUX + D + k) * RS + r] = rb[k];
 #pragma unroll
-        for (int c = 0; c < D; ++c) aux[(slot * NAUX + c) * RS + r] = img ? -u0[c] : u0[c];
+        for (int c = 0; c < D; ++c)
+            aux[(slot * NAUX + c) * RS + r] =
+                img < 0 ? u0[c] : real(2) * uw_param(a, img, c, real(0)) - u0[c];
         if (keep) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) o_df[i] = df[i];
@@ -189,9 +214,10 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
     };
 
     auto stage1 = [&](int q, bool keep_next) {
-        // beyond a wall: the image of the plane facing it (-1 -> 0, np -> np - 1)
-        const bool img = D > 1 && a.walls && (q < 0 || q >= np);
-        const int qq = (D == 1) ? 0 : (img ? (q < 0 ? -1 - q : 2 * np - 1 - q) : modp(q, np));
+        // beyond a wall: the image of the plane facing it (-1 -> 0, np -> np - 1);
+        // img = the wall crossed (0 lower, 1 upper), -1 for a fluid plane
+        const int img = (D > 1 && a.walls && (q < 0 || q >= np)) ? (q < 0 ? 0 : 1) : -1;
+        const int qq = (D == 1) ? 0 : (img >= 0 ? (q < 0 ? -1 - q : 2 * np - 1 - q) : modp(q, np));
         const int slot = slot_of(q);
         stage1_site(rxi, ryi, qq, slot, img, keep_next, n_df, n_bt, n_rho, n_j, n_E);
         if (tid < NRING) {

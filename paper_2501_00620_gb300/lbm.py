@@ -117,6 +117,7 @@ def _load():
     L.lbm_init.argtypes = [vp, ctypes.POINTER(lbm_fields_in)]
     L.lbm_step.argtypes = [vp, ctypes.c_long]
     L.lbm_set_force.argtypes = [vp, dp]
+    L.lbm_set_wall_velocity.argtypes = [vp, dp, dp]
     L.lbm_sync.argtypes = [vp]
     L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
     L.lbm_diagnostics.argtypes = [vp, dp]
@@ -146,7 +147,7 @@ def _load():
     L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
-    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_sync", "lbm_moments",
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
                  "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
                  "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
@@ -198,6 +199,12 @@ def lbm_init(sim, rho, u, T):
 
 def lbm_step(sim, n):
     _check(_lib.lbm_step(sim, int(n)))
+
+
+def lbm_set_wall_velocity(sim, lo, hi):
+    ll = None if lo is None else np.ascontiguousarray(lo, dtype=np.float64)
+    hh = None if hi is None else np.ascontiguousarray(hi, dtype=np.float64)
+    _check(_lib.lbm_set_wall_velocity(sim, _dp(ll), _dp(hh)))
 
 
 def lbm_set_force(sim, a):
@@ -354,6 +361,11 @@ class Simulation:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_wall_velocity(self, lo, hi):
+        """Velocities of the lower and upper walls (dim components each)."""
+        cut = lambda v: None if v is None else np.asarray(v, dtype=np.float64)[: self.dim]
+        lbm_set_wall_velocity(self.h, cut(lo), cut(hi))
 
     def set_force(self, a):
         """Uniform body-force acceleration (dim components; None removes it)."""

@@ -1,5 +1,5 @@
-"""Half-way bounce-back walls and the uniform body force on the GPU, against
-the FP64 oracle, through the C ABI (needs a GB300).
+"""Half-way bounce-back walls (at rest or moving) and the uniform body force
+on the GPU, against the FP64 oracle, through the C ABI (needs a GB300).
 
 FP64 storage: 1e-12 norm-wise on rho, T and the emitted populations and
 1e-12 absolute on u (units of c), as for the periodic lattices -- the wall
@@ -30,11 +30,17 @@ def _library_loaded():
         raise _IMPORT_ERROR
 
 
-def pair(d, shape, fields, tau, T0, thermal, bc, acc, dtype="f64", **kw):
+def pair(d, shape, fields, tau, T0, thermal, bc, acc, dtype="f64", uw=None, **kw):
+    """GPU and oracle lattices from the same fields.  Wall velocities are set
+    before the start: the oracle streams the start emission at init, the GPU
+    in its first step, and both then see the same walls."""
     nz, ny, nx = shape
     g = lbm.Simulation(d, nx, ny, nz, tau=tau, T0=T0, bc=bc, dtype=dtype, thermal=thermal, **kw)
-    g.init(*fields)
     o = oracle.Sim(d, nx, ny, nz, tau=tau, T0=T0, thermal=thermal, bc=bc)
+    if uw is not None:
+        g.set_wall_velocity(*uw)
+        o.set_wall_velocity(*uw)
+    g.init(*fields)
     o.init(*fields)
     if acc is not None:
         g.set_force(acc)
@@ -163,12 +169,60 @@ def test_walls_chunks_bitwise(d, shape):
                            tile=0, chunk=chunk)
         g.init(rho, u, T)
         g.set_force([1e-4] * d)
+        g.set_wall_velocity([0.02] + [0.0] * (d - 1), [-0.01] + [0.0] * (d - 1))
         g.step(9)
         f, b = g.emitted()
         if ref is None:
             ref = (f, b)
         else:
             assert np.array_equal(f, ref[0]) and np.array_equal(b, ref[1])
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("d", [2, 3])
+def test_moving_walls_fp64(d, thermal):
+    """Moving walls (Sec. III.D) with a force normal to them, against the
+    oracle: the bounced populations' wall momentum and the reflected image
+    velocity."""
+    shape = (1, 70, 300) if d == 2 else (24, 20, 40)
+    steps = 60 if d == 2 else 20
+    acc = (1e-4, -2e-4) if d == 2 else (0.0, 1e-4, -2e-4)
+    lo = (0.02, 0.0) if d == 2 else (0.01, 0.02, 0.0)
+    hi = (-0.01, 0.0) if d == 2 else (-0.01, 0.0, 0.0)
+    g, o = pair(d, shape, random_fields(d, shape, 6, 0.1), 0.6, 0.1, thermal, "walls", acc, uw=(lo, hi))
+    g.step(steps)
+    o.step(steps)
+    assert_parity(g, o)
+
+
+def test_couette_gravity_fp32_matches_oracle():
+    """FP32 storage, D2Q9 channel 64 x 32, walls at 0 and U, gravity normal
+    to them: the steady profile equals the FP64 oracle's (one column) to
+    1e-3 U."""
+    H, U, T, tau, g = 32, 0.02, 0.1, 0.6, -1e-3
+    steps = int(8 * H * H / (T * tau))
+    sim = lbm.Simulation(2, 64, H, tau=tau, T0=T, bc="walls", dtype="f32")
+    sim.set_wall_velocity([0.0, 0.0], [U, 0.0])
+    sim.init(1.0, np.zeros((2, 1, H, 64)), T)
+    sim.set_force([0.0, g])
+    sim.step(steps)
+    _, u, _ = sim.moments()
+    o = oracle.Sim(2, 1, H, tau=tau, T0=T, bc="walls")
+    o.set_wall_velocity([0.0, 0.0], [U, 0.0])
+    o.init(1.0, np.zeros((2, 1, H, 1)), T)
+    o.set_force([0.0, g])
+    o.step(steps)
+    _, uo, _ = o.moments()
+    assert np.abs(u[0] - uo[0]).max() < 1e-3 * U
+
+
+def test_wall_velocity_rejects_normal_component_and_no_walls():
+    w = lbm.Simulation(2, 16, 16, bc="walls")
+    with pytest.raises(Exception):
+        w.set_wall_velocity([0.0, 0.01], [0.0, 0.0])
+    p = lbm.Simulation(2, 16, 16)
+    with pytest.raises(Exception):
+        p.set_wall_velocity([0.01, 0.0], [0.0, 0.0])
 
 
 def test_walls_reject_1d():
