@@ -61,6 +61,9 @@ def lib():
         L.orc_set_force.argtypes = [ctypes.c_void_p, dp]
         L.orc_set_model.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_wall_velocity.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_set_mrt.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.orc_set_mrt.restype = ctypes.c_int
+        L.orc_moment_matrix.argtypes = [dp]
         L.orc_set_wall_velocity.restype = ctypes.c_int
         L.orc_set_model.restype = ctypes.c_int
         L.orc_std_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
@@ -116,6 +119,13 @@ def beq(d, u, T):
     uu = np.zeros(3)
     uu[:d] = np.asarray(u, dtype=np.float64)[:d]
     lib().orc_beq(d, _p(uu), float(T), _p(out))
+    return out
+
+
+def moment_matrix():
+    """Table M (Appendix B) with c = 1: the D3Q19 population-to-moment matrix."""
+    out = np.zeros((19, 19))
+    lib().orc_moment_matrix(_p(out))
     return out
 
 
@@ -179,6 +189,12 @@ class Sim:
 
     def step(self, n=1):
         lib().orc_step(self._h, int(n))
+
+    def set_mrt(self, s3, s4):
+        """MRT collision in the basis of Table M (D3Q19): rates of the third-
+        and fourth-order moments; the others relax at omega."""
+        if lib().orc_set_mrt(self._h, float(s3), float(s4)) != 0:
+            raise ValueError("oracle: MRT needs the D3Q19 bump scheme and rates in (0, 2)")
 
     def set_wall_velocity(self, lo, hi):
         """Tangential velocities of the lower and upper walls (d components)."""

@@ -75,6 +75,18 @@
  *       wall at equilibrium is reproduced); its bbar is unchanged.  The
  *       gradient stencil's image velocity is reflected about the wall's,
  *       2 u_w - u0.
+ *   R13 MRT collision (Appendix B; the paper itself runs SRT): D3Q19, in
+ *       the moment basis m of Table M.  The appendix leaves w_i and N^a
+ *       undefined: w_i are the lattice weights and N^a = 1 / sum_i w_i
+ *       (m^a_i)^2 -- the rows of Table M are orthogonal under the weighted
+ *       sum, so f_i = w_i sum_a m^a_i N^a M^a inverts M^a = sum_i m^a_i f_i.
+ *       Each moment relaxes at its own rate with the forcing weighted as in
+ *       the SRT step: M*^a = M^a + s_a (M^a_eq - M^a) + (1 - s_a/2) Phi^a,
+ *       Phi^a = sum_i m^a_i Phi_i; s_a = omega for the conserved and the
+ *       second-order rows (so eta = rho T tau and the energy of the thermal
+ *       mode are those of the SRT step), s3 for the third-order rows 10-15,
+ *       s4 for the fourth-order rows 16-18.  With s3 = s4 = omega it is the
+ *       SRT step (1 - omega/2 = omega tau).  bbar keeps the single rate.
  *   R10 Body force (Sec. III.A drives Poiseuille flow by a uniform
  *       acceleration a): the force density rho a joins the gradient force,
  *       F -> F + rho a, and its second-moment source joins G,
@@ -119,6 +131,8 @@ typedef struct {
     double tau, T0, omega;
     int thermal, bc;           /* bc: 0 periodic, 1 fixed-state in x, 2 walls (R9) */
     int model;                 /* 0 bump-function scheme, 1 standard comparator */
+    int mrt;                   /* 1: MRT collision in the basis of Table M (R13) */
+    double srate[QMAX];        /* its per-moment relaxation rates */
     double acc[3];             /* uniform body-force acceleration (R10) */
     double uw[2][3];           /* wall velocities (R12): [0] lower, [1] upper */
     long nstep;
@@ -150,6 +164,59 @@ static const int E3[19][3] = {
     {0, 0, 1},  {0, 0, -1}, {1, 1, 0},   {1, -1, 0},  {-1, 1, 0},
     {-1, -1, 0}, {1, 0, 1}, {1, 0, -1},  {-1, 0, 1},  {-1, 0, -1},
     {0, 1, 1},  {0, 1, -1}, {0, -1, 1},  {0, -1, -1}};
+
+/* Table M (Appendix B): the D3Q19 population-to-moment matrix with c = 1,
+ * row a = moment a, column i = population i in the order above.  Each row is
+ * written as integers over a common denominator (TM_DEN).                   */
+static const int TM_NUM[19][19] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 0, 0, 0, 0},
+    {0, 0, 1, 0, -1, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {-1, 2, -1, 2, -1, -1, -1, 2, 2, 2, 2, 2, 2, 2, 2, -1, -1, -1, -1},
+    {-1, -1, 2, -1, 2, -1, -1, 2, 2, 2, 2, -1, -1, -1, -1, 2, 2, 2, 2},
+    {-1, -1, -1, -1, -1, 2, 2, -1, -1, -1, -1, 2, 2, 2, 2, 2, 2, 2, 2},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 0, 0, 0, 0},
+    {0, 0, -2, 0, 2, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1},
+    {0, 0, 0, 0, 0, -2, 2, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, -1, -1, 1, 1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, -1, -1, 1, 1},
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, -1, 1},
+    {0, 1, 1, 1, 1, -2, -2, -2, -2, -2, -2, 1, 1, 1, 1, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0, 0, 0, -1, -1, -1, -1, 1, 1, 1, 1},
+    {1, -2, -2, -2, -2, -2, -2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1}};
+static const int TM_DEN[19] = {1, 1, 1, 1, 3, 3, 3, 1, 1, 1, 3, 3, 3, 1, 1, 1, 2, 2, 6};
+
+static double tm(int a, int i) { return (double)TM_NUM[a][i] / (double)TM_DEN[a]; }
+
+/* MRT collision of one site (R13): moments of f, f^eq and Phi, relaxation
+ * per moment, back to populations.                                        */
+static void mrt_collide(const orc_sim *s, const double *f, const double *fe, const double *phi, double *fs)
+{
+    const orc_lattice *L = &s->L;
+    double Ms[19];
+    for (int a = 0; a < 19; ++a) {
+        double M = 0.0, Me = 0.0, P = 0.0;
+        for (int i = 0; i < 19; ++i) {
+            M += tm(a, i) * f[i];
+            Me += tm(a, i) * fe[i];
+            P += tm(a, i) * phi[i];
+        }
+        Ms[a] = M + s->srate[a] * (Me - M) + (1.0 - 0.5 * s->srate[a]) * P;
+    }
+    for (int i = 0; i < 19; ++i) {
+        double acc = 0.0;
+        for (int a = 0; a < 19; ++a) {
+            double Na = 0.0;                       /* 1 / sum_k w_k m_ak^2 */
+            for (int k = 0; k < 19; ++k) Na += L->w[k] * tm(a, k) * tm(a, k);
+            acc += tm(a, i) * Ms[a] / Na;
+        }
+        fs[i] = L->w[i] * acc;
+    }
+}
 
 /* symmetric tensor component order: 1D (xx); 2D (xx, yy, xy);
  * 3D (xx, yy, zz, xy, xz, yz) */
@@ -479,8 +546,11 @@ static void phase_b(orc_sim *s)
         for (int k = 0; k < nb; ++k) s->G[n * nb + k] = G[k];
         const double *f = s->f + n * Q, *b = s->b + n * nb;
         double *fs = s->fs + n * Q, *bs = s->bs + n * nb;
-        for (int i = 0; i < Q; ++i)                        /* Eq. 55 */
-            fs[i] = f[i] + om * (fe[i] - f[i]) + om * tau * phi[i];
+        if (s->mrt)                                        /* R13 */
+            mrt_collide(s, f, fe, phi, fs);
+        else
+            for (int i = 0; i < Q; ++i)                    /* Eq. 55 */
+                fs[i] = f[i] + om * (fe[i] - f[i]) + om * tau * phi[i];
         for (int k = 0; k < nb; ++k)                       /* Eqs. 63, 65 */
             bs[k] = b[k] + om * (bq[k] - b[k]);
     }
@@ -733,6 +803,24 @@ int orc_set_wall_velocity(void *h, const double *lo, const double *hi)
         s->uw[1][a] = a < d ? hi[a] : 0.0;
     }
     return 0;
+}
+
+/* MRT collision (R13), D3Q19 bump scheme only: rates s3 (third-order
+ * moments) and s4 (fourth-order), each in (0, 2).  Returns 0 or -1.        */
+int orc_set_mrt(void *h, double s3, double s4)
+{
+    orc_sim *s = (orc_sim *)h;
+    if (s->L.d != 3 || s->model != 0 || !(s3 > 0 && s3 < 2) || !(s4 > 0 && s4 < 2)) return -1;
+    for (int a = 0; a < 19; ++a) s->srate[a] = a < 10 ? s->omega : (a < 16 ? s3 : s4);
+    s->mrt = 1;
+    return 0;
+}
+
+/* Table M with c = 1, row-major (19 x 19).  Test hook.                     */
+void orc_moment_matrix(double *out)
+{
+    for (int a = 0; a < 19; ++a)
+        for (int i = 0; i < 19; ++i) out[a * 19 + i] = tm(a, i);
 }
 
 /* Uniform body-force acceleration (R10), d components.                    */
