@@ -178,7 +178,7 @@ def hbm_peak():
         return 6800.0, "of fallback"
 
 
-KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_tma.cuh",
+KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_mrt.cuh", "lbm_tma.cuh",
                   "lbm_lean.cuh", "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
 
 
@@ -207,7 +207,8 @@ def _code_only(text):
 
 # the comparator kernel's own sources
 KERNEL_SOURCES_BY_KERNEL = {
-    "std_step_kernel": ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_std.cu"),
+    "std_step_kernel": ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_mrt.cuh",
+                        "lbm_std.cu"),
 }
 
 

@@ -173,6 +173,18 @@ lbm_status lbm_init(lbm_sim *sim, const lbm_fields_in *fields);
  * simulation's stream.  LBM_EINVAL for a NULL sim or a non-finite value. */
 lbm_status lbm_set_force(lbm_sim *sim, const double *a);
 
+/* MRT collision (Appendix B) for the D3Q19 bump scheme: moments in the basis
+ * of Table M, M^a = sum_i m^a_i f_i, relax at their own rates,
+ * M*^a = M^a + s_a (M^a_eq - M^a) + (1 - s_a/2) Phi^a, and populations come
+ * back as f_i = w_i sum_a m^a_i N^a M^a with N^a = 1 / sum_i w_i (m^a_i)^2.
+ * The conserved and second-order moments relax at omega (the viscosity
+ * eta = rho T tau of the SRT step); s3 is the rate of the third-order rows
+ * 10-15, s4 of the fourth-order rows 16-18; bbar keeps the single rate.
+ * s3 = s4 = omega is the SRT step; s3 <= 0 and s4 <= 0 switch MRT off.
+ * Runs on the generic kernel.  Waits for the simulation's stream.
+ * LBM_EINVAL for another lattice or model, or rates outside (0, 2). */
+lbm_status lbm_set_mrt(lbm_sim *sim, double s3, double s4);
+
 /* Velocities of the walls of an LBM_BC_WALLS lattice (Sec. III.D's Couette
  * flow): `lo` and `hi` point at dim host doubles each, the velocity of the
  * lower and upper wall (copied; NULL means at rest).  Walls move along

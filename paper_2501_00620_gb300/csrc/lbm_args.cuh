@@ -36,11 +36,17 @@ struct StepArgs {
     int walls_moving;     // 1: a wall has a nonzero (tangential) velocity
     double uw[2][3];      // wall velocities: [0] lower, [1] upper wall
     float uw_f[2][3];
+    int mrt;              // 1: MRT collision (D3Q19, lbm_mrt.cuh)
+    double mrt_s[2];      // its rates of the third- and fourth-order moments
+    float mrt_s_f[2];
 };
 
 // Body-force acceleration in the arithmetic type R.
 __host__ __device__ __forceinline__ double acc_param(const StepArgs& a, int c, double) { return a.acc[c]; }
 __host__ __device__ __forceinline__ float acc_param(const StepArgs& a, int c, float) { return a.acc_f[c]; }
+// MRT rate (0: third-order moments, 1: fourth-order) in the arithmetic type R.
+__host__ __device__ __forceinline__ double mrt_rate(const StepArgs& a, int k, double) { return a.mrt_s[k]; }
+__host__ __device__ __forceinline__ float mrt_rate(const StepArgs& a, int k, float) { return a.mrt_s_f[k]; }
 // Wall velocity (side 0 lower, 1 upper) in the arithmetic type R.
 __host__ __device__ __forceinline__ double uw_param(const StepArgs& a, int side, int c, double) { return a.uw[side][c]; }
 __host__ __device__ __forceinline__ float uw_param(const StepArgs& a, int side, int c, float) { return a.uw_f[side][c]; }

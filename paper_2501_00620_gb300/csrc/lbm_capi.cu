@@ -68,6 +68,8 @@ struct lbm_sim {
     bool forced = false;
     double uw[2][3] = {{0, 0, 0}, {0, 0, 0}};  // wall velocities (lower, upper)
     bool walls_moving = false;
+    bool mrt = false;  // MRT collision (D3Q19) with rates mrt_s
+    double mrt_s[2] = {0, 0};
     lbm_opts opts{};
     int dtype = 0;
     int device = 0;
@@ -146,6 +148,11 @@ StepArgs base_args(const lbm_sim* s) {
         a.acc_f[c] = (float)s->acc[c];
     }
     a.walls_moving = s->walls_moving ? 1 : 0;
+    a.mrt = s->mrt ? 1 : 0;
+    for (int k = 0; k < 2; ++k) {
+        a.mrt_s[k] = s->mrt_s[k];
+        a.mrt_s_f[k] = (float)s->mrt_s[k];
+    }
     for (int w = 0; w < 2; ++w)
         for (int c = 0; c < 3; ++c) {
             a.uw[w][c] = s->uw[w][c];
@@ -179,9 +186,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Walls and the body force are implemented in the generic kernel only: the
+// Walls, the body force and the MRT collision are implemented in the generic
+// kernel only: the
 // staged, strip and serving kernels serve periodic and fixed-state lattices.
-bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced; }
+bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced || s->mrt; }
 bool variant_allowed(const lbm_sim* s, int v) {
     if (!generic_only(s)) return true;
     return v < kTmaBase && !(s->D == 2 && v == 3);
@@ -741,6 +749,29 @@ lbm_status lbm_set_force(lbm_sim* s, const double* a) {
         }
     if (s->var >= 0 && !variant_allowed(s, s->var)) {
         s->var = -1;  // re-tune among the kernels that implement the force
+        s->multi_k = 0;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_mrt(lbm_sim* s, double s3, double s4) {
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    const bool on = s3 > 0 || s4 > 0;
+    if (on && (s->D != 3 || s->opts.model != LBM_MODEL_BUMP))
+        return fail(LBM_EINVAL, "the MRT collision needs the D3Q19 bump scheme");
+    if (on && !(s3 > 0 && s3 < 2 && s4 > 0 && s4 < 2)) return fail(LBM_EINVAL, "MRT rates must lie in (0, 2)");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));  // graphs captured the old arguments
+    s->mrt = on;
+    s->mrt_s[0] = on ? s3 : 0;
+    s->mrt_s[1] = on ? s4 : 0;
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    if (s->var >= 0 && !variant_allowed(s, s->var)) {
+        s->var = -1;  // re-tune among the kernels that implement it
         s->multi_k = 0;
     }
     return LBM_OK;

@@ -22,6 +22,9 @@
 // about the wall's, 2 u_w - u0 (Sec. III.D).
 // Body force (a.forced): F + rho a and G + rho (u a + a u) with the corrected
 // u = (j + F/2)/rho of Eq. 57.
+// MRT (a.mrt, D = 3): the SRT result is stored, then the difference of the
+// MRT step in the third- and fourth-order moments of Table M is added
+// (lbm_mrt.cuh).
 // The gradient needs rho*b on the neighbours, which exist only after the
 // neighbours have pulled; the ring is recomputed per tile and the kernel
 // marches along the slowest axis keeping three planes of (u0, rho b) in a
@@ -32,6 +35,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 
+#include "lbm_mrt.cuh"
 #include "lbm_site.cuh"
 
 namespace lbm {
@@ -269,6 +273,9 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
                 for (int d2 = c; d2 < D; ++d2) G[sym<D>(c, d2)] += ru[c] * ga[d2] + ru[d2] * ga[c];
         }
         site_collide<D, FS, real>(a, s, c_df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
+        if constexpr (D == 3) {
+            if (a.mrt && a.write_state) mrt_correct<FS, real>(a, s, c_df, c_rho, c_j, F);
+        }
     };
 
     auto carry = [&]() {

@@ -118,6 +118,7 @@ def _load():
     L.lbm_step.argtypes = [vp, ctypes.c_long]
     L.lbm_set_force.argtypes = [vp, dp]
     L.lbm_set_wall_velocity.argtypes = [vp, dp, dp]
+    L.lbm_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     L.lbm_sync.argtypes = [vp]
     L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
     L.lbm_diagnostics.argtypes = [vp, dp]
@@ -147,7 +148,7 @@ def _load():
     L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
-    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_sync", "lbm_moments",
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_set_mrt", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
                  "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
                  "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
@@ -199,6 +200,10 @@ def lbm_init(sim, rho, u, T):
 
 def lbm_step(sim, n):
     _check(_lib.lbm_step(sim, int(n)))
+
+
+def lbm_set_mrt(sim, s3, s4):
+    _check(_lib.lbm_set_mrt(sim, float(s3), float(s4)))
 
 
 def lbm_set_wall_velocity(sim, lo, hi):
@@ -361,6 +366,10 @@ class Simulation:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_mrt(self, s3, s4):
+        """MRT collision (D3Q19): rates of the third- and fourth-order moments."""
+        lbm_set_mrt(self.h, s3, s4)
 
     def set_wall_velocity(self, lo, hi):
         """Velocities of the lower and upper walls (dim components each)."""
