@@ -267,7 +267,9 @@ lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const ch
  * dtype, reservoirs, step counter, parameters) as a raw file with a small
  * header.  lbm_load requires a simulation created with the same dim, extents,
  * dtype and boundary.  A run of n steps equals n/2 steps + save + load + n/2
- * steps bit for bit. */
+ * steps bit for bit.  The body force, the wall velocities, the MRT rates and
+ * the model (lbm_opts.model) are settings of the simulation, not of the
+ * checkpoint: set them on the simulation that loads it. */
 lbm_status lbm_save(lbm_sim *sim, const char *path);
 lbm_status lbm_load(lbm_sim *sim, const char *path);
 

@@ -57,6 +57,34 @@ def test_argument_validation_needs_no_gpu(lib):
         assert e.value.status == lbm.LBM_EINVAL
 
 
+def test_boundary_model_and_setting_validation_needs_no_gpu(lib):
+    """Walls need dim 2 or 3; the comparator model runs on periodic lattices
+    with ny, nz <= 65535; unknown boundaries and models are refused; the
+    force, wall-velocity and MRT setters refuse a NULL simulation -- all on
+    the host, before any CUDA call."""
+    from paper_2501_00620_gb300 import lbm
+    bad = [((1, 64, 1, 1, 0.8, 0.3), dict(bc=lbm.LBM_BC_WALLS)),
+           ((2, 8, 8, 1, 0.8, 0.3), dict(bc=7))]
+    o = lbm.lbm_default_opts()
+    o.model = lbm.LBM_MODEL_STANDARD
+    bad += [((2, 8, 8, 1, 0.8, 0.3), dict(bc=lbm.LBM_BC_WALLS, opts=o)),
+            ((2, 8, 8, 1, 0.8, 0.3), dict(bc=lbm.LBM_BC_FIXED_STATE, opts=o)),
+            ((2, 8, 70000, 1, 0.8, 0.3), dict(bc=lbm.LBM_BC_PERIODIC, opts=o))]
+    o2 = lbm.lbm_default_opts()
+    o2.model = 5
+    bad.append(((2, 8, 8, 1, 0.8, 0.3), dict(bc=lbm.LBM_BC_PERIODIC, opts=o2)))
+    for args, kw in bad:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_create(*args, **kw)
+        assert e.value.status == lbm.LBM_EINVAL
+    for call in (lambda: lbm.lbm_set_force(None, [1e-4, 0.0]),
+                 lambda: lbm.lbm_set_wall_velocity(None, [0.01, 0.0], [0.0, 0.0]),
+                 lambda: lbm.lbm_set_mrt(None, 1.2, 1.2)):
+        with pytest.raises(lbm.LBMError) as e:
+            call()
+        assert e.value.status == lbm.LBM_EINVAL
+
+
 def test_noalloc_step_rejects_before_any_cuda_call(lib):
     """The no-allocation step validates its sizes on the host first: a lattice
     needing more diagnostics scratch than the fixed array holds is refused
