@@ -13,7 +13,8 @@ bump scheme's is rho T tau (Eq. 84).
   T0: T0 tau k^2) -- the paper's central contrast;
 * sound travels at sqrt(T0) (pressure rho T0);
 * mass and momentum are conserved to round-off;
-* at T0 = cs2 the bump scheme reduces to the comparator to O(A^2) on D2Q9.
+* at T0 = cs2 the bump scheme reduces to the comparator to O(A^2) on D2Q9;
+* between moving walls the comparator's plane Couette profile is exactly linear.
 """
 import numpy as np
 import pytest
@@ -127,3 +128,17 @@ def test_bump_reduces_to_standard_at_cs2():
         out[T] = (np.abs(r["bump"][0] - r["standard"][0]).max(), np.abs(r["bump"][1] - r["standard"][1]).max())
     assert max(out[1 / 3]) < 10 * A * A
     assert out[0.2][1] > 0.1 * A
+
+
+def test_std_couette_linear_exact():
+    """The comparator between moving half-way bounce-back walls: the plane
+    Couette profile is exactly linear (the textbook property of this wall
+    rule), as for the bump scheme."""
+    H, U = 24, 0.02
+    s = oracle.Sim(2, 1, H, tau=0.6, T0=1 / 3, bc="walls", model="standard")
+    s.set_wall_velocity([0.0, 0.0], [U, 0.0])
+    s.init(1.0, np.zeros((2, 1, H, 1)), 1 / 3)
+    s.step(int(8 * H * H / (0.6 / 3)))
+    _, u, _ = s.moments()
+    z = np.arange(H) + 0.5
+    assert np.abs(u[0].ravel() - U * z / H).max() < 1e-10 * U
