@@ -107,3 +107,29 @@ def test_noalloc_step_rejects_before_any_cuda_call(lib):
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_step_noalloc(1, 8, 1, 1, 0.8, 0.3, 0, buf[0], buf[1], buf[0], buf[3])
     assert "differ" in str(e.value)
+
+
+def test_binding_structs_match_the_headers(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    the C compiler gives the header's struct (gcc on the host)."""
+    from paper_2501_00620_gb300 import lbm
+    structs = [lbm.lbm_opts, lbm.lbm_fields_in, lbm.lbm_fields_out, lbm.lbm_server_opts,
+               lbm.lbm_request, lbm.lbm_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm_serve.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert int(got["%s.%s" % (name, f[0])]) == getattr(st, f[0]).offset, (name, f[0])
