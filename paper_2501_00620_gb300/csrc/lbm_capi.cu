@@ -541,6 +541,25 @@ lbm_status build_graph(lbm_sim* s, int parity, int steps) {
     return LBM_OK;
 }
 
+// The captured graphs hold the step arguments of their capture: after a
+// setting changes they are dropped and captured again at the next step.
+void drop_graphs(lbm_sim* s) {
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+}
+
+// A setting only the generic kernel implements (walls, force, MRT) sends a
+// lattice tuned onto another kernel back to the autotuner.
+void retune_if_needed(lbm_sim* s) {
+    if (s->var >= 0 && !variant_allowed(s, s->var)) {
+        s->var = -1;
+        s->multi_k = 0;
+    }
+}
+
 lbm_status check_flag(lbm_sim* s) {
     int h = 0;
     CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -742,15 +761,8 @@ lbm_status lbm_set_force(lbm_sim* s, const double* a) {
     CK(cudaStreamSynchronize(s->stream));
     for (int c = 0; c < 3; ++c) s->acc[c] = v[c];
     s->forced = v[0] != 0 || v[1] != 0 || v[2] != 0;
-    for (int k = 0; k < 2; ++k)
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
-    if (s->var >= 0 && !variant_allowed(s, s->var)) {
-        s->var = -1;  // re-tune among the kernels that implement the force
-        s->multi_k = 0;
-    }
+    drop_graphs(s);
+    retune_if_needed(s);
     return LBM_OK;
 }
 
@@ -765,15 +777,8 @@ lbm_status lbm_set_mrt(lbm_sim* s, double s3, double s4) {
     s->mrt = on;
     s->mrt_s[0] = on ? s3 : 0;
     s->mrt_s[1] = on ? s4 : 0;
-    for (int k = 0; k < 2; ++k)
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
-    if (s->var >= 0 && !variant_allowed(s, s->var)) {
-        s->var = -1;  // re-tune among the kernels that implement it
-        s->multi_k = 0;
-    }
+    drop_graphs(s);
+    retune_if_needed(s);
     return LBM_OK;
 }
 
@@ -799,11 +804,7 @@ lbm_status lbm_set_wall_velocity(lbm_sim* s, const double* lo, const double* hi)
             moving = moving || v[w][c] != 0;
         }
     s->walls_moving = moving;
-    for (int k = 0; k < 2; ++k)
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
+    drop_graphs(s);
     return LBM_OK;
 }
 
@@ -1114,11 +1115,7 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     long long ctr = h.nstep;
     CK(cudaMemcpy(s->step_ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));
     CK(cudaMemset(s->flag, 0, sizeof(int)));
-    for (int k = 0; k < 2; ++k)
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
+    drop_graphs(s);
     return LBM_OK;
 }
 
