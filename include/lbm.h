@@ -266,10 +266,12 @@ lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const ch
 /* Checkpoint: write / read the full state (emitted planes in the storage
  * dtype, reservoirs, step counter, parameters) as a raw file with a small
  * header.  lbm_load requires a simulation created with the same dim, extents,
- * dtype and boundary.  A run of n steps equals n/2 steps + save + load + n/2
- * steps bit for bit.  The body force, the wall velocities, the MRT rates and
- * the model (lbm_opts.model) are settings of the simulation, not of the
- * checkpoint: set them on the simulation that loads it. */
+ * dtype, boundary and model (lbm_opts.model; LBM_EINVAL otherwise), and
+ * refuses with LBM_EIO a file whose header holds tau or T0 that are not
+ * finite and > 0.  A run of n steps equals n/2 steps + save + load + n/2
+ * steps bit for bit.  The body force, the wall velocities and the MRT rates
+ * are settings of the simulation, not of the checkpoint: set them on the
+ * simulation that loads it. */
 lbm_status lbm_save(lbm_sim *sim, const char *path);
 lbm_status lbm_load(lbm_sim *sim, const char *path);
 
@@ -288,7 +290,7 @@ lbm_status lbm_load(lbm_sim *sim, const char *path);
  *   b_in, b_out: nb planes of N doubles, bbar* + I/3 (the diagonal planes
  *                shifted by 1/3, the off-diagonal planes unchanged);
  * with the plane and site order of lbm_get_state.  f_in/b_in hold the state
- * at step t, f_out/b_out receive step t+1; input and output must not overlap.
+ * at step t, f_out/b_out receive step t+1.
  * diag_out (device pointer or NULL) receives dim+2 doubles: mass, momentum
  * and energy of the state at step t, as lbm_diagnostics gives them.
  * tau, T0 and thermal are those of lbm_create_ex; stream is a cudaStream_t
@@ -304,10 +306,14 @@ lbm_status lbm_load(lbm_sim *sim, const char *path);
  * each, 268 M sites), 26,208 in 3D (32 x 8 x 64 sites each, 429 M sites).
  * A larger lattice is rejected with LBM_EINVAL and a message.  The call sets
  * the ticket and flag to zero on `stream` before each launch; the partial
- * sums need no clearing.  The first call on a device (with that device
- * current) looks up the array's device address with cudaGetSymbolAddress and
- * sets the kernels' shared-memory attribute; make that first call before
- * any stream capture.  The array is shared by all calls on one device, so
+ * sums need no clearing.  Every call looks up the array's device address
+ * with cudaGetSymbolAddress (so a device reset between calls is harmless);
+ * the first call on a device, and the first after a reset, also sets the
+ * kernels' shared-memory attribute: make that first call before any stream
+ * capture.  input and output must not overlap: an output range that overlaps
+ * an input or the other output (byte ranges of Q*N and nb*N doubles) is
+ * rejected with LBM_EINVAL; the two inputs may alias each other.  The array
+ * is shared by all calls on one device, so
  * two calls that overlap in time on one device -- from two host threads, or
  * on two streams -- race on it and may return wrong diagnostics or flags. */
 lbm_status lbm_step_noalloc(int dim, int nx, int ny, int nz, double tau, double T0, int thermal,

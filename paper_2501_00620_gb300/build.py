@@ -55,14 +55,34 @@ def _stamp(extra=""):
     return h.hexdigest()
 
 
-def _compile(src, verbose):
+def _headers_digest():
+    h = hashlib.sha256()
+    for f in _headers():
+        h.update(f.encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _compile(src, verbose, headers_digest):
+    """Compile one translation unit unless its object was built from the same
+    source, headers and flags (a stamp beside the object)."""
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    h = hashlib.sha256()
+    with open(src, "rb") as fh:
+        h.update(fh.read())
+    h.update((headers_digest + " ".join(ARCH + NVCC_FLAGS) + str(verbose)).encode())
+    stamp = obj + ".stamp"
+    if not verbose and os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == h.hexdigest():
+        return obj, ""
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+    with open(stamp, "w") as fh:
+        fh.write(h.hexdigest())
     return obj, r.stderr
 
 
@@ -77,8 +97,9 @@ def build(force=False, verbose=False, jobs=None):
     srcs = _sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     logs = {}
+    hd = _headers_digest()
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        futs = {ex.submit(_compile, s, verbose): s for s in srcs}
+        futs = {ex.submit(_compile, s, verbose, hd): s for s in srcs}
         objs = []
         for fu in cf.as_completed(futs):
             obj, log = fu.result()

@@ -199,7 +199,13 @@ bool variant_allowed(const lbm_sim* s, int v) {
 // extents, and rows whose byte length is a multiple of 16 (tensor strides).
 bool tma_applicable(const lbm_sim* s, int v) {
     if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64 || generic_only(s)) return false;
-    if (v - kTmaBase >= n_tma_variants(s->D)) return false;
+    if (v >= kPairBase) {
+        // the pair kernel: FP32 storage, periodic lattices
+        if (v - kPairBase >= n_pair_variants(s->D)) return false;
+        if (s->dtype != DT_F32 || s->bc != LBM_BC_PERIODIC) return false;
+    } else if (v - kTmaBase >= n_tma_variants(s->D)) {
+        return false;
+    }
     Variant t = variant(s->D, v);
     if (s->nx % t.tx != 0) return false;
     if (s->D == 3 && s->ny % t.ty != 0) return false;
@@ -464,6 +470,8 @@ lbm_status autotune(lbm_sim* s) {
             if (variant_allowed(s, v)) vars.push_back(v);
         for (int k = 0; k < n_tma_variants(s->D); ++k)
             if (tma_applicable(s, kTmaBase + k)) vars.push_back(kTmaBase + k);
+        for (int k = 0; k < n_pair_variants(s->D); ++k)
+            if (tma_applicable(s, kPairBase + k)) vars.push_back(kPairBase + k);
     }
     std::vector<int> chunks = s->opts.chunk > 0 ? std::vector<int>{s->opts.chunk} : chunk_candidates(s);
     if (vars.size() * chunks.size() == 1) {
@@ -1020,10 +1028,12 @@ lbm_status lbm_set_state(lbm_sim* s, const double* f, const double* b) {
 }
 
 // Checkpoint file: header, then the emitted planes in the storage dtype, then
-// the reservoirs (fixed-state boundary only).
+// the reservoirs (fixed-state boundary only).  `model` is lbm_opts.model: a
+// bump-scheme state and a comparator state have the same planes but do not
+// mean the same thing, so a load across models is refused.
 struct CkptHeader {
     char magic[8];
-    int D, nx, ny, nz, dtype, bc, thermal, pad;
+    int D, nx, ny, nz, dtype, bc, thermal, model;
     double tau, T0;
     long long nstep;
 };
@@ -1058,6 +1068,7 @@ lbm_status lbm_save(lbm_sim* s, const char* path) {
     h.dtype = s->dtype;
     h.bc = s->bc;
     h.thermal = s->opts.thermal;
+    h.model = s->opts.model;
     h.tau = s->tau;
     h.T0 = s->T0;
     h.nstep = s->nstep;
@@ -1083,6 +1094,17 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     if (h.D != s->D || h.nx != s->nx || h.ny != s->ny || h.nz != s->nz || h.dtype != s->dtype || h.bc != s->bc) {
         std::fclose(fp);
         return fail(LBM_EINVAL, "checkpoint does not match this simulation");
+    }
+    if (h.model != s->opts.model) {
+        std::fclose(fp);
+        return fail(LBM_EINVAL, "checkpoint holds the state of another model (lbm_opts.model)");
+    }
+    // the same checks lbm_create_ex applies: a corrupt or foreign file must
+    // not set a meaningless omega = 1/(tau + 1/2)
+    if (!std::isfinite(h.tau) || !(h.tau > 0) || !std::isfinite(h.T0) || !(h.T0 > 0) || (h.thermal != 0 && h.thermal != 1) ||
+        h.nstep < 0) {
+        std::fclose(fp);
+        return fail(LBM_EIO, "checkpoint header holds invalid parameters (tau, T0, thermal or step count)");
     }
     const long long N = s->N;
     size_t fb = (size_t)s->Q * N * fbytes_of(s->dtype), bb = (size_t)s->NB * N * rbytes_of(s->dtype);

@@ -77,14 +77,20 @@ __device__ __forceinline__ void mrt_correct(const StepArgs& a, long long s, cons
     }
     FS* __restrict__ fo = static_cast<FS*>(a.fout);
     const long long N = a.N;
+    bool finite = true;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         R corr = R(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
             if (mrt_hi(k, i) != 0) corr += R(mrt_hi(k, i)) * c[k];
-        Store<FS>::st(fo, (long long)i * N + s, R(ld_own(fo, (long long)i * N + s)) + R(L::w(i)) * corr);
+        const R v = R(ld_own(fo, (long long)i * N + s)) + R(L::w(i)) * corr;
+        finite = finite && isfinite(v);
+        Store<FS>::st(fo, (long long)i * N + s, v);
     }
+    // the corrected populations are the stored state: a non-finite one is
+    // reported by this step, as site_collide reports its own
+    if (!finite) atomicOr(a.flag, 1);
 }
 
 }  // namespace lbm

@@ -14,6 +14,7 @@
 // file-scope device array g_noalloc_scratch below instead of in buffers
 // the library allocates.  Every GPU that loads the library holds this array
 // (kNoallocScratchBytes) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -42,11 +43,42 @@ constexpr int kChunk = 64;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch per device
+// Per device: the context in which the kernels' shared-memory attribute was
+// set.  A device reset (cudaDeviceReset) ends that context; the next call on
+// the device runs in a new one, whose ID differs, and sets it again.
+struct DeviceSetup {
+    unsigned long long ctx_id = 0;  // 0: not set up
+};
+DeviceSetup g_setup[kMaxDevices];
 
 lbm_status fail(lbm_status s, const std::string& m) {
     lbm::set_last_error(m);  // reported by lbm_last_error()
     return s;
+}
+
+// Unique ID of the current context (driver entry points through the runtime,
+// so the library needs no link to libcuda).
+cudaError_t current_context_id(unsigned long long* id) {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* p1 = nullptr;
+        void* p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !p1 || !p2)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<GetCurrent>(p1);
+        get_id = reinterpret_cast<GetId>(p2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+    return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
 }
 
 template <int D, int TX, int TY>
@@ -56,23 +88,29 @@ cudaError_t set_smem_attr() {
                                 (int)Sh::smem);
 }
 
-// One-time set-up per device (with that device current): look up the device
-// address of the scratch array -- in host code the array's name is only a
-// host-side stand-in -- and allow the kernels' dynamic shared memory.
+// Set-up per call (with the device current): look up the device address of
+// the scratch array -- in host code the array's name is only a host-side
+// stand-in -- which also makes the device's primary context current; then,
+// once per device and context, allow the kernels' dynamic shared memory.
+// The address is looked up on every call, so it is never stale.
 lbm_status setup_device(int dev, void** out) {
     std::lock_guard<std::mutex> g(g_mu);
     if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device ordinal out of range");
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("current context: ") + cudaGetErrorString(e));
+    DeviceSetup& d = g_setup[dev];
+    if (d.ctx_id != id) {
         e = set_smem_attr<1, 256, 1>();
         if (e == cudaSuccess) e = set_smem_attr<2, 128, 1>();
         if (e == cudaSuccess) e = set_smem_attr<3, 32, 8>();
         if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+        d.ctx_id = id;
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return LBM_OK;
 }
 
@@ -105,12 +143,25 @@ lbm_status lbm_step_noalloc(int dim, int nx, int ny, int nz, double tau, double 
         return fail(LBM_EINVAL, "invalid lattice extents");
     if (!(tau > 0) || !(T0 > 0)) return fail(LBM_EINVAL, "tau and T0 must be > 0");
     if (!f_in || !b_in || !f_out || !b_out) return fail(LBM_EINVAL, "NULL state buffer");
-    if (f_in == f_out || b_in == b_out) return fail(LBM_EINVAL, "input and output buffers must differ");
     const size_t nblocks = blocks_needed(dim, nx, ny, nz);
     if (nblocks > max_blocks(dim))
         return fail(LBM_EINVAL, "lattice too large for the no-allocation step: needs " + std::to_string(nblocks) +
                                     " blocks of diagnostics scratch, the fixed array holds " +
                                     std::to_string(max_blocks(dim)));
+    {
+        // The step reads f_in, b_in while it writes f_out, b_out: an output
+        // that overlaps any of the four buffers (in part, or a b plane inside
+        // an f buffer) would race.  The two inputs may alias each other.
+        const int Q = dim == 1 ? 3 : (dim == 2 ? 9 : 19), NB = dim == 1 ? 1 : (dim == 2 ? 3 : 6);
+        const size_t N = (size_t)nx * ny * nz;
+        const uintptr_t lo[4] = {(uintptr_t)f_in, (uintptr_t)b_in, (uintptr_t)f_out, (uintptr_t)b_out};
+        const size_t len[4] = {Q * N * sizeof(double), NB * N * sizeof(double), Q * N * sizeof(double),
+                               NB * N * sizeof(double)};
+        for (int o = 2; o < 4; ++o)
+            for (int k = 0; k < 4; ++k)
+                if (k != o && lo[o] < lo[k] + len[k] && lo[k] < lo[o] + len[o])
+                    return fail(LBM_EINVAL, "output buffers must not overlap each other or the inputs");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -134,9 +185,7 @@ lbm_status lbm_step_noalloc(int dim, int nx, int ny, int nz, double tau, double 
     a.nz = nz;
     a.chunk = kChunk;
     a.N = (long long)nx * ny * nz;
-    a.omega = 1.0 / (tau + 0.5);
-    a.tau = tau;
-    a.T0 = T0;
+    lbm::set_step_params(a, tau, T0);
     a.thermal = thermal ? 1 : 0;
     a.fixed_x = 0;
     a.rows = (long long)ny * nz;

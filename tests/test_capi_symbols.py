@@ -104,9 +104,21 @@ def test_noalloc_step_rejects_before_any_cuda_call(lib):
             lbm.lbm_step_noalloc(*args, *buf)
         assert e.value.status == lbm.LBM_EINVAL
         assert msg in str(e.value)
-    with pytest.raises(lbm.LBMError) as e:
-        lbm.lbm_step_noalloc(1, 8, 1, 1, 0.8, 0.3, 0, buf[0], buf[1], buf[0], buf[3])
-    assert "differ" in str(e.value)
+    # D1Q3, 8 sites: f planes 3 x 64 bytes, b plane 64 bytes
+    fb, bb = 3 * 8 * 8, 8 * 8
+    base = 1 << 20
+    f_in, b_in, f_out, b_out = base, base + 4096, base + 8192, base + 12288
+    overlapping = [
+        (f_in, b_in, f_in, b_out),                 # output = input
+        (f_in, b_in, f_out, b_in + 8),             # b_out partly over b_in
+        (f_in, b_in, f_in + fb - 8, b_out),        # f_out starts inside f_in
+        (f_in, b_in, f_out, f_in + 16),            # a b plane inside an f buffer
+        (f_in, b_in, f_out, f_out + fb - bb // 2),  # the two outputs overlap
+    ]
+    for ptrs in overlapping:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_step_noalloc(1, 8, 1, 1, 0.8, 0.3, 0, *ptrs)
+        assert e.value.status == lbm.LBM_EINVAL and "overlap" in str(e.value), ptrs
 
 
 def test_binding_structs_match_the_headers(tmp_path):
