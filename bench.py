@@ -209,6 +209,8 @@ def _code_only(text):
 KERNEL_SOURCES_BY_KERNEL = {
     "std_step_kernel": ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_mrt.cuh",
                         "lbm_std.cu"),
+    "step_pair_kernel": ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_tma.cuh", "lbm_lean.cuh",
+                         "lbm_f2.cuh", "lbm_step_pair.cuh", "lbm_pair_launch.cuh"),
 }
 
 

@@ -1,6 +1,7 @@
 // Dimension dispatch for the kernel launchers.
 #include "lbm_internal.h"
 #include "lbm_fast_launch.cuh"
+#include "lbm_pair_launch.cuh"
 
 namespace lbm {
 
@@ -42,13 +43,19 @@ int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_v
 
 const char* kernel_name(int D, int v) {
     if (v == kStdVariant) return "std_step_kernel";
+    if (v >= kPairBase) return "step_pair_kernel";
     if (v >= kTmaBase) return "step_fast_kernel";
     return (D == 2 && v == 3) ? "step_strip_kernel" : "step_kernel";
 }
 
 int n_tma_variants(int D) { return D == 2 ? n_fast_variants_d2() : (D == 3 ? n_fast_variants_d3() : 0); }
+int n_pair_variants(int D) { return D == 2 ? n_pair_variants_d2() : (D == 3 ? n_pair_variants_d3() : 0); }
 
 Variant variant(int D, int v) {
+    if (v >= kPairBase && v < kStdVariant) {
+        const int k = v - kPairBase;
+        return D == 2 ? pair_variant_d2(k) : (D == 3 ? pair_variant_d3(k) : Variant{0, 0});
+    }
     if (v >= kTmaBase) {
         const int k = v - kTmaBase;
         return D == 2 ? fast_variant_d2(k) : (D == 3 ? fast_variant_d3(k) : Variant{0, 0});
@@ -57,6 +64,10 @@ Variant variant(int D, int v) {
 }
 
 cudaError_t tma_box(int D, int dtype, int v, TmaBox* box) {
+    if (v >= kPairBase) {
+        const int kk = v - kPairBase;
+        return D == 2 ? pair_box_d2(dtype, kk, box) : (D == 3 ? pair_box_d3(dtype, kk, box) : cudaErrorInvalidValue);
+    }
     const int k = v - kTmaBase;
     return D == 2 ? fast_box_d2(dtype, k, box) : (D == 3 ? fast_box_d3(dtype, k, box) : cudaErrorInvalidValue);
 }
@@ -70,6 +81,11 @@ size_t step_smem(int D, int dtype, int v) {
 }
 
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
+    if (v >= kPairBase) {
+        const int kk = v - kPairBase;
+        return D == 2 ? launch_step_pair_d2(dtype, kk, ta, st)
+                      : (D == 3 ? launch_step_pair_d3(dtype, kk, ta, st) : cudaErrorInvalidValue);
+    }
     const int k = v - kTmaBase;
     return D == 2 ? launch_step_fast_d2(dtype, k, ta, st)
                   : (D == 3 ? launch_step_fast_d3(dtype, k, ta, st) : cudaErrorInvalidValue);

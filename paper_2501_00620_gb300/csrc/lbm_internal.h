@@ -23,6 +23,10 @@ constexpr int kStripNT = 256;
 // kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;
 
+// kPairBase + k selects the k-th tile of the pair kernel (lbm_step_pair.cuh):
+// FP32 storage, periodic lattices.
+constexpr int kPairBase = 200;
+
 // Variant index of the standard-lattice comparator kernel (lbm_std.cu).
 constexpr int kStdVariant = 1000;
 
@@ -38,6 +42,7 @@ int n_variants(int D);
 // Name of the kernel template variant v launches (for reports).
 const char* kernel_name(int D, int v);
 int n_tma_variants(int D);
+int n_pair_variants(int D);
 Variant variant(int D, int v);
 size_t step_smem(int D, int dtype, int v);
 cudaError_t tma_box(int D, int dtype, int v, TmaBox* box);

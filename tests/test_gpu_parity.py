@@ -243,6 +243,39 @@ def test_checkpoint_resume_bitwise():
     assert c.nstep == 30
 
 
+def test_checkpoint_refuses_other_model_and_bad_parameters():
+    """lbm_load refuses a bump-scheme checkpoint on a comparator simulation
+    (same planes, other meaning), and a header whose tau or T0 is not finite
+    and > 0 (a corrupt or foreign file), before touching the state."""
+    import struct
+    rho, u, T = W.taylor_green_pulse_2d(32)
+    a = lbm.Simulation(2, 32, 32, tau=0.6, T0=1 / 3, dtype="f32")
+    a.init(rho, u, T)
+    a.step(2)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "ck.bin")
+        a.save(p)
+        s = lbm.Simulation(2, 32, 32, tau=0.6, T0=1 / 3, dtype="f32", model="standard")
+        with pytest.raises(lbm.LBMError) as e:
+            s.load(p)
+        assert e.value.status == lbm.LBM_EINVAL and "model" in str(e.value)
+        raw = bytearray(open(p, "rb").read())
+        # header: magic[8], 8 ints, then tau and T0 as doubles
+        for off, bad in ((40, 0.0), (40, float("nan")), (48, -0.1), (48, float("inf"))):
+            q = os.path.join(d, "bad.bin")
+            patched = bytearray(raw)
+            patched[off:off + 8] = struct.pack("<d", bad)
+            open(q, "wb").write(bytes(patched))
+            b = lbm.Simulation(2, 32, 32, tau=0.6, T0=1 / 3, dtype="f32")
+            b.init(rho, u, T)
+            with pytest.raises(lbm.LBMError) as e:
+                b.load(q)
+            assert e.value.status == lbm.LBM_EIO
+            b.close()
+        s.close()
+    a.close()
+
+
 def test_state_roundtrip():
     rho, u, T = W.taylor_green_pulse_2d(32)
     g = lbm.Simulation(2, 32, 32, tau=0.6, T0=0.1, thermal=True)
@@ -401,6 +434,73 @@ def test_fp32_diagnostics_match_exact_state_sums(d, shape):
         mom = np.array([(e[:, a].reshape((-1,) + (1,) * (f.ndim - 1)) * f).sum() for a in range(d)])
         assert np.abs(diag[1:1 + d] - mom).max() / mass < 1e-8
         g.close()
+
+
+PAIR_BASE = 200
+N_PAIR = {2: 1, 3: 3}  # pair-kernel tiles per lattice
+
+
+@pytest.mark.parametrize("d,shape", [(3, (24, 32, 64)), (3, (9, 8, 128)), (2, (1, 40, 256)), (2, (1, 24, 128))])
+@pytest.mark.parametrize("thermal", [True, False])
+def test_pair_kernel_matches_generic(d, shape, thermal):
+    """The pair kernel (two x-adjacent sites per thread in packed FP32x2,
+    8-byte population accesses, TMA-staged variance planes, tensor-memory
+    hand-off) computes what the generic kernel computes up to FP32 rounding,
+    for several chunk lengths and one or several tiles per axis; one step of
+    it matches the FP64 oracle to the storage precision on sampled windows;
+    and its diagnostics equal FP64 sums of the stored state."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(13)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((d,) + shape)
+    T = 0.1 * (1 + 0.05 * rng.random(shape))
+    T0, tau = 0.1, 0.6
+    ref = lbm.Simulation(d, nx, ny, nz, tau=tau, T0=T0, dtype="f32", thermal=thermal, tile=0, chunk=4)
+    ref.init(rho, u, T)
+    ref.step(7)
+    fr, br = ref.emitted()
+    # chunk 20: a segment of 22 planes, so the pipeline barriers of the
+    # warp-specialized form serve three planes each
+    for k, chunk in [(k, c) for k in range(N_PAIR[d]) for c in (3, 8, 20)]:
+        g = lbm.Simulation(d, nx, ny, nz, tau=tau, T0=T0, dtype="f32", thermal=thermal,
+                           tile=PAIR_BASE + k, chunk=chunk)
+        g.init(rho, u, T)
+        g.step(6)
+        assert g.launch_config()[0] == PAIR_BASE + k
+        f0, b0 = g.emitted()
+        g.step(1)
+        f1, b1 = g.emitted()
+        diag = g.diagnostics()
+        g.sync()
+        assert normwise(f1, fr) < 2e-5 and np.abs(b1 - br).max() < 2e-5
+        wf, wb = check_windows(d, f0, b0, f1, b1, tau, T0, thermal, n_windows=3, half=4)
+        assert wf < 2e-6 and wb < 2e-6
+        mass = f1.sum()
+        assert abs(diag[0] - mass) / mass < 1e-9
+        e, _ = oracle.lattice(d)
+        mom = np.array([(e[:, a].reshape((-1,) + (1,) * (f1.ndim - 1)) * f1).sum() for a in range(d)])
+        assert np.abs(diag[1:1 + d] - mom).max() / mass < 1e-8
+        g.close()
+
+
+def test_pair_kernel_moments_match_generic():
+    """lbm_moments through the pair kernel (write_state off, FP64 moments
+    out) gives the corrected u and T of the generic kernel up to FP32
+    rounding."""
+    shape = (12, 16, 128)
+    rng = np.random.default_rng(17)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((3,) + shape)
+    T = 0.1 * (1 + 0.05 * rng.random(shape))
+    out = []
+    for tile in (0, PAIR_BASE):
+        g = lbm.Simulation(3, 128, 16, 12, tau=0.6, T0=0.1, dtype="f32", thermal=True, tile=tile, chunk=4)
+        g.init(rho, u, T)
+        g.step(4)
+        out.append(g.moments())
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() < 2e-5
 
 
 STRIP_TILE = 3
