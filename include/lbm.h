@@ -185,6 +185,24 @@ lbm_status lbm_set_force(lbm_sim *sim, const double *a);
  * LBM_EINVAL for another lattice or model, or rates outside (0, 2). */
 lbm_status lbm_set_mrt(lbm_sim *sim, double s3, double s4);
 
+/* FP64 recovery of the temperature where it is small (thermal mode, 32/16-bit
+ * storage; the paper's T of Eq. 57 and the T_unc of Eq. 68 taken from the
+ * moments).  T = (Ebar - rho |u|^2) / (d rho) is a difference of two nearly
+ * equal numbers when T << |u|^2, so in FP32 its relative error grows like
+ * |u|^2 / T.  With kappa > 0, a site whose FP32 T_unc is below
+ * kappa |u0|^2 repeats its variance transport (Eq. 66), moments and rho b
+ * (Eq. 68) in FP64, and its corrected T and b^eq (Appendix A) come from the
+ * FP64 energy; the bump parameters are then rounded to the storage type.
+ * lbm_moments reports that FP64 T.  kappa = 0 (the default) turns it off.
+ * Runs on the generic kernel (the staged kernels do not carry FP64 values
+ * between their stages); each recovered site costs about 150 FP64
+ * operations, which on GB300 take the time of several thousand FP32 ones,
+ * so kappa should select only the sites that need it (kappa = 1: T below
+ * |u|^2).  No effect for FP64 storage or isothermal runs.  A setting of
+ * the simulation, not of a checkpoint.  Waits for the simulation's stream.
+ * LBM_EINVAL for kappa < 0 or not finite. */
+lbm_status lbm_set_small_t(lbm_sim *sim, double kappa);
+
 /* Velocities of the walls of an LBM_BC_WALLS lattice (Sec. III.D's Couette
  * flow): `lo` and `hi` point at dim host doubles each, the velocity of the
  * lower and upper wall (copied; NULL means at rest).  Walls move along
@@ -274,6 +292,22 @@ lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const ch
  * simulation that loads it. */
 lbm_status lbm_save(lbm_sim *sim, const char *path);
 lbm_status lbm_load(lbm_sim *sim, const char *path);
+
+/* Test switches (library service, no counterpart in the paper): they
+ * exercise the failure paths of the kernels without faulting the GPU.
+ * LBM_DEBUG_MISSING_COPY: in the next steps, one thread block of the
+ * shared-memory-staged kernels (launch variants 100.. and 200..) arms the
+ * transaction barrier of its first variance-plane copy but issues no copy.
+ * Every wait on that barrier gives up after its time limit (20 ms), the
+ * block leaves without storing, after its copies in flight have completed,
+ * and the step reports LBM_ETIMEOUT at the next lbm_sync / lbm_moments /
+ * lbm_diagnostics.  The state is then not a valid step: lbm_init or lbm_load
+ * it again (lbm_init also clears the device flag).  The generic kernel has
+ * no staged copies and ignores the switch.  flags = 0 turns it off.  Waits
+ * for the simulation's stream; drops the captured step graphs.
+ * LBM_EINVAL for unknown flags. */
+#define LBM_DEBUG_MISSING_COPY 1
+lbm_status lbm_set_debug(lbm_sim *sim, int flags);
 
 /* One time step that allocates no device memory, on device buffers the
  * caller owns.  The paper has no counterpart: this is a library service for

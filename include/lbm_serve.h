@@ -3,11 +3,17 @@
  * the bump-function lattice Boltzmann method (arXiv 2501.00620) on one GPU.
  *
  * The paper has no counterpart: this is a library service on top of the
- * method.  Each request is one simulation -- D1Q3 or D2Q9, FP32 storage,
- * periodic or fixed-state boundary, given initial fields (rho, u, T) and a
- * step count -- and its result is the macroscopic fields (rho, u, T; Eq. 57
- * and the moment temperature) after those steps, the same quantities
- * lbm_moments returns.
+ * method.  Each request is one simulation -- D1Q3 or D2Q9, periodic or
+ * fixed-state boundary, given initial fields (rho, u, T) and a step count --
+ * and its result is the macroscopic fields (rho, u, T; Eq. 57 and the moment
+ * temperature) after those steps, the same quantities lbm_moments returns.
+ *
+ * Precision: FP32 storage and arithmetic, except for 1D fixed-state requests
+ * (two-state Riemann problems), which run with FP64 storage and arithmetic:
+ * in FP32 the rounding-size perturbations at a shock front of such a problem
+ * grow until the state leaves the physical range (rho <= 0, measured after
+ * about 1600 steps on the 4096-site problem), while requests may ask for
+ * thousands of steps; from FP64 rounding they stay small over that span.
  *
  * Model:
  *  - lbm_server_submit copies the request's fields and queues it; a service

@@ -36,6 +36,10 @@ struct StepArgs {
     int walls_moving;     // 1: a wall has a nonzero (tangential) velocity
     double uw[2][3];      // wall velocities: [0] lower, [1] upper wall
     float uw_f[2][3];
+    int debug_missing_copy;  // 1: block (0,0,0) of a staged kernel arms its first variance-copy barrier
+                             // without issuing the copy (exercises the bounded waits; nothing is left in flight)
+    double small_t;       // > 0 (thermal, 32/16-bit storage): sites with T < small_t |u|^2 recover T in FP64
+    float small_t_f;
     int mrt;              // 1: MRT collision (D3Q19, lbm_mrt.cuh)
     double mrt_s[2];      // its rates of the third- and fourth-order moments
     float mrt_s_f[2];

@@ -69,6 +69,8 @@ struct lbm_sim {
     double uw[2][3] = {{0, 0, 0}, {0, 0, 0}};  // wall velocities (lower, upper)
     bool walls_moving = false;
     bool mrt = false;  // MRT collision (D3Q19) with rates mrt_s
+    int debug = 0;     // LBM_DEBUG_* flags (lbm_set_debug)
+    double small_t = 0;  // lbm_set_small_t: FP64 temperature recovery where T < small_t |u|^2
     double mrt_s[2] = {0, 0};
     lbm_opts opts{};
     int dtype = 0;
@@ -149,6 +151,9 @@ StepArgs base_args(const lbm_sim* s) {
     }
     a.walls_moving = s->walls_moving ? 1 : 0;
     a.mrt = s->mrt ? 1 : 0;
+    a.debug_missing_copy = (s->debug & LBM_DEBUG_MISSING_COPY) ? 1 : 0;
+    a.small_t = s->small_t;
+    a.small_t_f = (float)s->small_t;
     for (int k = 0; k < 2; ++k) {
         a.mrt_s[k] = s->mrt_s[k];
         a.mrt_s_f[k] = (float)s->mrt_s[k];
@@ -186,10 +191,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// Walls, the body force and the MRT collision are implemented in the generic
-// kernel only: the
+// Walls, the body force, the MRT collision and the FP64 small-T recovery are
+// implemented in the generic kernel only: the
 // staged, strip and serving kernels serve periodic and fixed-state lattices.
-bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced || s->mrt; }
+bool small_t_on(const lbm_sim* s) { return s->small_t > 0 && s->opts.thermal && s->dtype != DT_F64; }
+bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced || s->mrt || small_t_on(s); }
 bool variant_allowed(const lbm_sim* s, int v) {
     if (!generic_only(s)) return true;
     return v < kTmaBase && !(s->D == 2 && v == 3);
@@ -790,6 +796,27 @@ lbm_status lbm_set_mrt(lbm_sim* s, double s3, double s4) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_small_t(lbm_sim* s, double kappa) {
+    if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (!(kappa >= 0) || !std::isfinite(kappa)) return fail(LBM_EINVAL, "kappa must be finite and >= 0");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));  // graphs captured the old arguments
+    s->small_t = kappa;
+    drop_graphs(s);
+    retune_if_needed(s);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_debug(lbm_sim* s, int flags) {
+    if (!s) return fail(LBM_EINVAL, "NULL sim");
+    if (flags & ~LBM_DEBUG_MISSING_COPY) return fail(LBM_EINVAL, "unknown debug flag");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    s->debug = flags;
+    drop_graphs(s);  // captured launches hold the old arguments
+    return LBM_OK;
+}
+
 lbm_status lbm_set_wall_velocity(lbm_sim* s, const double* lo, const double* hi) {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     if (s->bc != LBM_BC_WALLS) return fail(LBM_EINVAL, "wall velocities need LBM_BC_WALLS");
@@ -1137,6 +1164,8 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     long long ctr = h.nstep;
     CK(cudaMemcpy(s->step_ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));
     CK(cudaMemset(s->flag, 0, sizeof(int)));
+    // a step that gave up (LBM_ETIMEOUT) left the reduction ticket counted short
+    CK(cudaMemset(s->ticket, 0, 64));
     drop_graphs(s);
     return LBM_OK;
 }

@@ -6,6 +6,8 @@
 // second moment per axis).
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_args.cuh"
 #include "lbm_lattice.cuh"
 
@@ -248,9 +250,40 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R*
 // bad |= 1: rho <= 0 or non-finite; bad |= 2: T <= 0 in thermal mode.
 // I is the index type of the site (int where the lattice has fewer than 2^31
 // sites); Acc the diagnostics accumulator (DiagAcc or a kernel's own).
+// FP64 temperature of the corrected moments (Eq. 57, thermal mode) from the
+// site's pulled populations df, its energy Ebar (E64, summed in FP64 with
+// an FP64 variance transport) and the FP32 gradients F, tr G:
+// T = (Ebar + tr G / 2 - rho |u|^2) / (D rho), u = (j0 + F/2) / rho.  Used
+// where T << |u|^2, where the FP32 difference cancels.
+template <int D>
+__device__ __forceinline__ double temperature64(const float* df, double E64, const float* F, float trG) {
+    using L = Lattice<D>;
+    double r = 1.0, j[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) j[c] = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const double d = df[i];
+        r += d;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (L::e(i, c) != 0) j[c] += L::e(i, c) * d;
+    }
+    double uu = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double u = (j[c] + 0.5 * (double)F[c]) / r;
+        uu += u * u;
+    }
+    return (E64 + 0.5 * (double)trG - r * uu) / (D * r);
+}
+
+// E64: the site's Ebar summed in FP64 where stage 1 found T small (then T is
+// recovered in FP64 here too); E64 < 0 marks "no FP64 value".
 template <int D, typename FS, typename R, typename I = long long, typename Acc = DiagAcc<R, D + 2>>
 __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_df, const R* c_bt, R rho,
-                                             const R* c_j, R c_E, const R* F, const R* G, Acc& acc, int& bad) {
+                                             const R* c_j, R c_E, const R* F, const R* G, Acc& acc, int& bad,
+                                             double E64 = -1.0) {
     using L = Lattice<D>;
     using breal = typename Store<FS>::breal;
     const I N = (I)a.N;
@@ -267,7 +300,15 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_
         uu += u[c] * u[c];
     }
     const R Ecorr = c_E + R(0.5) * trG;
-    const R Tm = (Ecorr - rho * uu) * irho * R(1.0 / D);
+    R Tm = (Ecorr - rho * uu) * irho * R(1.0 / D);
+    double Tm64 = double(Tm);
+    if constexpr (std::is_same<R, float>::value) {
+        // small T: recover T in FP64 (the FP32 difference above cancels)
+        if (E64 >= 0.0 && a.thermal) {
+            Tm64 = temperature64<D>(c_df, E64, F, trG);
+            Tm = float(Tm64);
+        }
+    }
     const R T = a.thermal ? Tm : T0;
     // fatal: the method divides by rho; non-finite values propagate
     if (!(rho > R(0)) || !isfinite(Ecorr) || !isfinite(uu)) bad |= 1;
@@ -287,7 +328,7 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_
         a.mout[s] = double(rho);
 #pragma unroll
         for (int c = 0; c < D; ++c) a.mout[(1 + c) * N + s] = double(u[c]);
-        a.mout[(1 + D) * N + s] = double(Tm);
+        a.mout[(1 + D) * N + s] = Tm64;
     }
     if (!a.write_state) return;
     collide_store<D, FS, R, I>(static_cast<FS*>(a.fout) + s, N, c_df, rho, u, F, G, trG, omega, tau);

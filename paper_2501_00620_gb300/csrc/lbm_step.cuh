@@ -34,6 +34,7 @@
 
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_mrt.cuh"
 #include "lbm_site.cuh"
@@ -119,6 +120,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
     // interior values carried from stage 1 of plane p to stage 2 of plane p
     real c_df[Q], c_bt[NB], c_rho, c_j[D], c_E;
     real n_df[Q], n_bt[NB], n_rho, n_j[D], n_E;
+    double c_E64 = -1.0, n_E64 = -1.0;  // FP64 Ebar of a small-T site (32/16-bit storage), else -1
 
     DiagAcc<real, D + 2> acc;
     int bad = 0;
@@ -154,16 +156,11 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
                 for (int k = 0; k < Q; ++k) rho_self += Store<FS>::ld(fin, (long long)k * N + self);
             }
         }
-        real df[Q], bsum[NB];
-#pragma unroll
-        for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        // source of population i: its stored value and the variance it carries
+        auto fetch = [&](int i, real& v, real* bv) {
             int sx = gx - L::e(i, 0);
             int sy = (D >= 2) ? wrap1(gy - L::e(i, 1), ny) : 0;
             int sz = (D == 3) ? wrap1(gz - L::e(i, 2), nz) : 0;
-            real v;
-            real bv[NB];
             const int sm = (D == 3) ? gz - L::e(i, 2) : gy - L::e(i, 1);
             if (D > 1 && a.walls && (sm < 0 || sm >= np)) {
                 // half-way bounce-back: the site's own opposite emission,
@@ -192,6 +189,14 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 #pragma unroll
                 for (int k = 0; k < NB; ++k) bv[k] = real(__ldg(bin + BLayout<D, FS>::at(k, s, N)));
             }
+        };
+        real df[Q], bsum[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) bsum[k] = real(-0.0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            real v, bv[NB];
+            fetch(i, v, bv);
             df[i] = v;
             const real fi = real(L::w(i)) + v;
 #pragma unroll
@@ -199,6 +204,67 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
         }
         real bt[NB], rho, j[D], E, u0[D], rb[NB];
         site_moments<D, real>(df, bsum, omega, T0, a.thermal, bt, rho, j, E, u0, rb);
+        double E64 = -1.0;
+        if constexpr (std::is_same<real, float>::value) {
+            if (a.thermal && a.small_t_f > 0.0f) {
+                real uu = real(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c) uu += u0[c] * u0[c];
+                const real Tu = (E - rho * uu) / (real(D) * rho);
+                if (Tu < a.small_t_f * uu) {
+                    // T << |u|^2: the transport (Eq. 66), the moments and
+                    // rho b (Eq. 68) again in FP64 from the same sources
+                    double bs[NB], r = 1.0, jj[D], e = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) bs[k] = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) jj[c] = 0.0;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        real v, bv[NB];
+                        fetch(i, v, bv);
+                        const double d = v, fi = L::w(i) + d;
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) bs[k] += fi * (double)bv[k];
+                        r += d;
+#pragma unroll
+                        for (int c = 0; c < D; ++c)
+                            if (L::e(i, c) != 0) jj[c] += L::e(i, c) * d;
+                        e += (norm2<D>(i) - D * (1.0 / 3.0)) * d;
+                    }
+                    double b64[NB], tr = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) b64[k] = bs[k] / r;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) tr += b64[c];
+                    e += r * tr;
+                    double u64[D], q = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        u64[c] = jj[c] / r;
+                        q += u64[c] * u64[c];
+                    }
+                    const double Tu64 = (e - r * q) / (D * r);
+                    const double hw = 0.5 * a.omega;
+#pragma unroll
+                    for (int c = 0; c < D; ++c)
+#pragma unroll
+                        for (int d2 = c; d2 < D; ++d2) {
+                            const int k = sym<D>(c, d2);
+                            const double beq = u64[c] * u64[d2] / 3.0 + (c == d2 ? Tu64 : 0.0);
+                            double v = r * (b64[k] - hw * (b64[k] - beq));
+                            if (c == d2) v -= r / 3.0;
+                            rb[k] = real(v);
+                        }
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) bt[k] = real(b64[k]);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) u0[c] = real(u64[c]);
+                    E = real(e);
+                    E64 = e;
+                }
+            }
+        }
 #pragma unroll
         for (int k = 0; k < NB; ++k) aux[(slot * NAUX + D + k) * RS + r] = rb[k];
 #pragma unroll
@@ -206,6 +272,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
             aux[(slot * NAUX + c) * RS + r] =
                 img < 0 ? u0[c] : real(2) * uw_param(a, img, c, real(0)) - u0[c];
         if (keep) {
+            n_E64 = E64;
 #pragma unroll
             for (int i = 0; i < Q; ++i) o_df[i] = df[i];
 #pragma unroll
@@ -272,7 +339,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 #pragma unroll
                 for (int d2 = c; d2 < D; ++d2) G[sym<D>(c, d2)] += ru[c] * ga[d2] + ru[d2] * ga[c];
         }
-        site_collide<D, FS, real>(a, s, c_df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
+        site_collide<D, FS, real>(a, s, c_df, c_bt, c_rho, c_j, c_E, F, G, acc, bad, c_E64);
         if constexpr (D == 3) {
             if (a.mrt && a.write_state) mrt_correct<FS, real>(a, s, c_df, c_rho, c_j, F);
         }
@@ -287,6 +354,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
 #pragma unroll
         for (int c = 0; c < D; ++c) c_j[c] = n_j[c];
         c_E = n_E;
+        c_E64 = n_E64;
     };
 
     if (D == 1) {

@@ -218,6 +218,8 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     __device__ __forceinline__ void issue_b(int q) {
         const int bs = bs_of(q);
         mbar_arrive_expect_tx(bbar() + bs, Sh::BBYTES);
+        if (a.debug_missing_copy && q == p0 - 2 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+            return;  // armed, never filled: every wait on this slot runs into its time limit
         const int plane = wrapq(q);
         if (D == 3)  // pair planes: x in floats of the (2 nx)-wide pair rows
             tma_load_4d(bslot(bs), &ta.bmap, bbar() + bs, 2 * (x0 - PXB), y0 - 2, plane, 0);

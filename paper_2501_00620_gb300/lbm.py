@@ -119,6 +119,8 @@ def _load():
     L.lbm_set_force.argtypes = [vp, dp]
     L.lbm_set_wall_velocity.argtypes = [vp, dp, dp]
     L.lbm_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.lbm_set_debug.argtypes = [vp, ctypes.c_int]
+    L.lbm_set_small_t.argtypes = [vp, ctypes.c_double]
     L.lbm_sync.argtypes = [vp]
     L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
     L.lbm_diagnostics.argtypes = [vp, dp]
@@ -148,7 +150,7 @@ def _load():
     L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
-    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_set_mrt", "lbm_sync", "lbm_moments",
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_set_mrt", "lbm_set_debug", "lbm_set_small_t", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
                  "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
                  "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
@@ -204,6 +206,17 @@ def lbm_step(sim, n):
 
 def lbm_set_mrt(sim, s3, s4):
     _check(_lib.lbm_set_mrt(sim, float(s3), float(s4)))
+
+
+LBM_DEBUG_MISSING_COPY = 1
+
+
+def lbm_set_small_t(sim, kappa):
+    _check(_lib.lbm_set_small_t(sim, float(kappa)))
+
+
+def lbm_set_debug(sim, flags):
+    _check(_lib.lbm_set_debug(sim, int(flags)))
 
 
 def lbm_set_wall_velocity(sim, lo, hi):
@@ -370,6 +383,14 @@ class Simulation:
     def set_mrt(self, s3, s4):
         """MRT collision (D3Q19): rates of the third- and fourth-order moments."""
         lbm_set_mrt(self.h, s3, s4)
+
+    def set_small_t(self, kappa):
+        """FP64 temperature recovery where T < kappa |u|^2 (thermal, 32/16-bit storage)."""
+        lbm_set_small_t(self.h, kappa)
+
+    def set_debug(self, flags):
+        """Test switches of the staged kernels (LBM_DEBUG_MISSING_COPY)."""
+        lbm_set_debug(self.h, flags)
 
     def set_wall_velocity(self, lo, hi):
         """Velocities of the lower and upper walls (dim components each)."""

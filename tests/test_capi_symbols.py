@@ -79,7 +79,9 @@ def test_boundary_model_and_setting_validation_needs_no_gpu(lib):
         assert e.value.status == lbm.LBM_EINVAL
     for call in (lambda: lbm.lbm_set_force(None, [1e-4, 0.0]),
                  lambda: lbm.lbm_set_wall_velocity(None, [0.01, 0.0], [0.0, 0.0]),
-                 lambda: lbm.lbm_set_mrt(None, 1.2, 1.2)):
+                 lambda: lbm.lbm_set_mrt(None, 1.2, 1.2),
+                 lambda: lbm.lbm_set_debug(None, lbm.LBM_DEBUG_MISSING_COPY),
+                 lambda: lbm.lbm_set_small_t(None, 1.0)):
         with pytest.raises(lbm.LBMError) as e:
             call()
         assert e.value.status == lbm.LBM_EINVAL

@@ -503,6 +503,84 @@ def test_pair_kernel_moments_match_generic():
         assert np.abs(a - b).max() < 2e-5
 
 
+@pytest.mark.parametrize("tile", [TMA_BASE + 4, PAIR_BASE, PAIR_BASE + 2])
+def test_bounded_copy_wait_times_out_and_context_survives(tile):
+    """A staged kernel whose first variance copy in one block is armed on its
+    transaction barrier but never issued (the LBM_DEBUG_MISSING_COPY switch;
+    nothing is left in flight) gives up after the bounded wait, drains,
+    frees its tensor memory and returns: the host sees LBM_ETIMEOUT, and the
+    same context then runs ordinary steps that equal a fresh simulation's."""
+    shape = (12, 16, 64)
+    rng = np.random.default_rng(23)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((3,) + shape)
+    T = 0.1 * np.ones(shape)
+    g = lbm.Simulation(3, 64, 16, 12, tau=0.6, T0=0.1, dtype="f32", tile=tile, chunk=4)
+    g.init(rho, u, T)
+    g.step(1)  # tuned onto the requested tile
+    assert g.launch_config()[0] == tile
+    g.set_debug(lbm.LBM_DEBUG_MISSING_COPY)
+    g.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.sync()
+        g.diagnostics()
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    g.set_debug(0)
+    g.init(rho, u, T)
+    g.step(3)
+    f, b = g.emitted()
+    ref = lbm.Simulation(3, 64, 16, 12, tau=0.6, T0=0.1, dtype="f32", tile=tile, chunk=4)
+    ref.init(rho, u, T)
+    ref.step(3)
+    fr, br = ref.emitted()
+    assert np.array_equal(f, fr) and np.array_equal(b, br)
+    g.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_small_t_fp64_recovery(d):
+    """T0 = 0.02 with |u| ~ 0.3 (T << |u|^2): the FP32 temperature
+    T = (Ebar - rho |u|^2)/(d rho) cancels (relative error ~1e-7 here).  With
+    the FP64 recovery on (lbm_set_small_t) the transport, rho, j0 and Ebar
+    of the site are FP64 sums of the stored FP32 values, so what is left of
+    the error against the FP64 oracle on the same stored state is the FP32
+    rounding of the gradient sums F, G (Eqs. 59, 61; on a uniform lattice
+    their FP32 sums cancel only to ~eps |u| |rho b|): measured 3e-8 / 2e-9 /
+    2e-8 against 4e-7 / 2e-7 / 1e-7 in 1D / 2D / 3D.  Velocity and density
+    agree either way."""
+    n = 16
+    shape = (n,) * d + (1,) * (3 - d)
+    shape = shape[::-1]
+    rho = np.full(shape, 1.03)
+    u = np.zeros((d,) + shape)
+    for c, v in enumerate((0.27, 0.11, -0.07)[:d]):
+        u[c] = v
+    T = np.full(shape, 0.02)
+    nz, ny, nx = shape
+    g = lbm.Simulation(d, nx, ny, nz, tau=0.6, T0=0.02, thermal=True, dtype="f32", tile=0, chunk=4)
+    g.init(rho, u, T)
+    g.step(2)
+    f, b = g.emitted()
+    o = oracle.Sim(d, nx, ny, nz, tau=0.6, T0=0.02, thermal=True)
+    o.set_emitted(f, b)
+    orho, ou, oT = o.moments()
+    _, _, T_off = g.moments()
+    g.set_small_t(1.0)
+    grho, gu, T_on = g.moments()
+    err_on = np.abs(T_on - oT).max() / np.abs(oT).max()
+    err_off = np.abs(T_off - oT).max() / np.abs(oT).max()
+    assert err_on < 1e-7 and err_on < err_off / 3, (err_on, err_off)
+    assert np.abs(grho - orho).max() < 1e-6 and np.abs(gu - ou).max() < 1e-6
+    # the step with the recovery on stays a valid step of the same lattice
+    g.step(2)
+    f2, b2 = g.emitted()
+    o.step(2)
+    fo, bo = o.emitted()
+    assert normwise(f2, fo) < 1e-6 and np.abs(b2 - bo).max() < 1e-6
+    g.close()
+
+
 STRIP_TILE = 3
 
 

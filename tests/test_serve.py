@@ -5,9 +5,11 @@
   mix of uneven requests sharing the batched launches.
 * A request that arrives while another is running joins the running batch
   and finishes first when it is shorter.
-* Results agree with the single-simulation entry points (same FP32 storage
-  and arithmetic: within 1e-6 of the field scale) and with the FP64 oracle
+* Results agree with the single-simulation entry points (same storage and
+  arithmetic: within 1e-6 of the field scale) and with the FP64 oracle
   within FP32 accumulation error (1e-5 after 200 steps of a sound wave).
+* 1D Riemann requests run in FP64 (the server's precision policy): the
+  longest ones of the seeded mix stay physical and match the oracle.
 * Admission respects the device-memory budget: requests wait for room and
   the pool is empty again at the end.
 """
@@ -88,7 +90,9 @@ def test_matches_single_simulation(req):
     tau, T0, thermal, bc = W.request_params(req)
     # the server runs 1D requests on the generic tile body (tile 0) and 2D
     # requests on the strip kernel's body (tile 3), 16 rows per work item
-    sim = lbm.Simulation(req["dim"], req["nx"], req["ny"], 1, tau=tau, T0=T0, bc=bc, dtype="f32",
+    # storage of the server's precision policy: FP64 for 1D fixed-state requests
+    dtype = "f64" if (req["dim"] == 1 and bc == "fixed") else "f32"
+    sim = lbm.Simulation(req["dim"], req["nx"], req["ny"], 1, tau=tau, T0=T0, bc=bc, dtype=dtype,
                          thermal=thermal, tile=3 if req["dim"] == 2 else 0, chunk=16)
     sim.init(rho, u, T)
     sim.step(req["steps"])
@@ -114,6 +118,42 @@ def test_matches_oracle_sound_wave():
     assert normwise(rho_s, orr[0]) < 1e-5
     assert np.abs(u_s - ou[:, 0]).max() < 1e-5
     assert normwise(T_s, oT[0]) < 1e-5
+
+
+def _long_riemann_requests():
+    """1D Riemann requests of the seeded serving mix (BASELINE config 5): the
+    three with the most steps among lattices of at most 2048 sites, and the
+    two with the most steps per site (the shock reflects from the frozen
+    reservoirs many times) -- the requests that left the physical range
+    when the server ran them in FP32."""
+    r1 = [r for r in W.serving_requests() if r["dim"] == 1 and r["kind"] == "riemann" and r["nx"] <= 2048]
+    by_steps = sorted(r1, key=lambda r: -r["steps"])[:3]
+    by_ratio = [r for r in sorted(r1, key=lambda r: -r["steps"] / r["nx"]) if r not in by_steps][:2]
+    return by_steps + by_ratio
+
+
+@pytest.mark.parametrize("req", _long_riemann_requests(), ids=lambda r: "id%d_nx%d_steps%d" % (r["id"], r["nx"], r["steps"]))
+def test_long_riemann_requests_stay_physical_and_match_oracle(req):
+    """Under the server's precision policy (FP64 for 1D fixed-state requests)
+    the longest Riemann requests of the mix finish without leaving the
+    physical range and match the FP64 oracle within the tolerance of the
+    two-state problem at thousands of steps (1e-6: the shock amplifies the
+    rounding-order difference of two FP64 implementations)."""
+    srv = lbm.Server(hbm_budget=1 << 28)
+    res = srv.wait(submit(srv, req))
+    srv.close()
+    assert not res.unstable
+    rho_s, u_s, T_s, _ = res
+    rho, u, T = W.request_fields(req)
+    tau, T0, thermal, bc = W.request_params(req)
+    o = oracle.Sim(1, req["nx"], 1, 1, tau=tau, T0=T0, thermal=thermal, bc=bc)
+    o.init(rho, u, T)
+    o.step(req["steps"])
+    orr, ou, oT = o.moments()
+    assert (rho_s > 0).all() and np.isfinite(T_s).all()
+    assert normwise(rho_s, orr[0]) < 1e-6
+    assert np.abs(u_s - ou[:, 0]).max() < 1e-6
+    assert normwise(T_s, oT[0]) < 1e-6
 
 
 def test_budget_limits_admission():
