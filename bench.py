@@ -416,8 +416,21 @@ def run_serve(args):
         tickets.append(submit(srv, r))
     results = [srv.wait(t, timeout=3600.0) for t in tickets]
     lat = np.array([r[3] for r in results])
-    unstable = [dict(kind=q["kind"], dim=q["dim"], nx=q["nx"], steps=q["steps"])
+    unstable = [dict(id=q["id"], kind=q["kind"], dim=q["dim"], nx=q["nx"], steps=q["steps"])
                 for q, r in zip(reqs, results) if r.unstable]
+    # requests on which the FP64 oracle itself leaves the physical range (a
+    # list written by tests/golden/make_riemann_mix_oracle.py for the seeded
+    # 1000-request mix)
+    oracle_fatal = set()
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "riemann_mix_oracle.txt")) as fh:
+            for ln in fh:
+                if ln.strip() and not ln.startswith("#"):
+                    rid, _, _, fatal = (int(v) for v in ln.split())
+                    if fatal:
+                        oracle_fatal.add(rid)
+    except OSError:
+        pass
     st = srv.stats()
     clocks = sampler.stop()
     srv.close()
@@ -468,6 +481,9 @@ def run_serve(args):
                     "max_s": float(lat.max()), "wall_s": wall, "busy_s": busy, "rounds": rounds,
                     "offered_mlups": updates / max(reqs[-1]["t_arrival"], 1e-9) / 1e6,
                     "unstable_requests": len(unstable),
+                    "unstable_also_in_fp64_oracle": (sum(1 for q in unstable if q["id"] in oracle_fatal)
+                                                     if len(reqs) == 1000 else None),
+                    "fp64_oracle_unstable_in_mix": len(oracle_fatal) if len(reqs) == 1000 else None,
                     "unstable_examples": unstable[:5],
                     "sequential": seq},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -133,6 +133,17 @@ typedef struct {
                                0: off */
     int use_graphs;         /* 1 (default): lbm_step replays CUDA graphs */
     int model;              /* LBM_MODEL_BUMP (default) or LBM_MODEL_STANDARD */
+    int halo;               /* 0 (default); 2: the simulation is one slab of a
+                               lattice decomposed along its slowest axis (y in
+                               2D, z in 3D): that axis ends in 2 halo planes on
+                               each side, which the step reads but does not
+                               update, and nothing wraps along it.  The extent
+                               passed to lbm_create_ex includes the 4 halo
+                               planes.  The halo holds the neighbouring slabs'
+                               emitted state (lbm_halo_exchange or
+                               lbm_halo_pack / lbm_halo_unpack after every
+                               step).  2D/3D bump scheme, periodic or
+                               fixed-state boundary in x */
 } lbm_opts;
 
 typedef struct lbm_sim lbm_sim;
@@ -292,6 +303,41 @@ lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const ch
  * simulation that loads it. */
 lbm_status lbm_save(lbm_sim *sim, const char *path);
 lbm_status lbm_load(lbm_sim *sim, const char *path);
+
+/* Domain decomposition (slabs along the slowest axis; no counterpart in the
+ * paper, whose step is a nearest-neighbour stencil).  A site's update reads
+ * the emitted state of its neighbours (the pull, Eq. 49, and the transport,
+ * Eq. 66) and, through the gradient of rho b (Eqs. 59, 61, 68), of the
+ * neighbours of its neighbours: a slab needs the two planes beyond each of
+ * its faces, refreshed after every step.  Slabs are simulations created with
+ * lbm_opts.halo = 2: with h = 2 and n planes along the slowest axis, planes
+ * [0, h) and [n - h, n) are the halo and [h, n - h) are owned.  lbm_init of
+ * a slab takes fields for all n planes (the halo from the neighbouring
+ * slabs, as the whole lattice's fields give them); lbm_moments writes the
+ * owned planes only; lbm_diagnostics sums the owned sites (the lattice's
+ * totals are the sums over slabs, one all-reduce of dim + 2 doubles).
+ *
+ * lbm_halo_bytes: bytes of one message -- h planes of every population and
+ * variance plane in the storage type (0 for a simulation without halo).
+ * lbm_halo_pack: copies the outermost h owned planes on `side` (0: low,
+ * planes h .. 2h-1; 1: high, planes n-2h .. n-h-1) of the current state into
+ * `dst` (device memory of lbm_halo_bytes bytes), asynchronously on the
+ * simulation's stream.  lbm_halo_unpack: writes `src` (a message packed by
+ * the neighbour on that side) into the halo planes on `side` (0: planes
+ * 0 .. h-1, 1: planes n-h .. n-1).  Between processes a message travels from
+ * one slab's pack to the next slab's unpack (point-to-point, e.g. NCCL
+ * send / recv); both calls only enqueue copies.
+ * lbm_halo_exchange: the same exchange among k slabs held by this process
+ * (one or several devices), periodic along the slowest axis: slab i's low
+ * halo receives slab i-1's top owned planes, its high halo slab i+1's
+ * bottom ones (indices mod k).  Device-to-device copies ordered by events
+ * after each slab's last step and before its next one; call it after every
+ * lbm_step(sim, 1) of all slabs.  Slabs must agree in dim, cross-section,
+ * storage and halo depth (LBM_EINVAL otherwise). */
+size_t lbm_halo_bytes(const lbm_sim *sim);
+lbm_status lbm_halo_pack(lbm_sim *sim, int side, void *dst);
+lbm_status lbm_halo_unpack(lbm_sim *sim, int side, const void *src);
+lbm_status lbm_halo_exchange(lbm_sim *const *sims, int k);
 
 /* Test switches (library service, no counterpart in the paper): they
  * exercise the failure paths of the kernels without faulting the GPU.

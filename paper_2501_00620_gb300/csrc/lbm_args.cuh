@@ -10,6 +10,9 @@ struct StepArgs {
     void* bout;           // NB planes
     int nx, ny, nz;
     int chunk;            // planes per block along the march axis
+    int halo;             // 0, or 2: the march axis (y in 2D, z in 3D) ends in two halo planes at each
+                          // side that the step reads but does not update, and nothing wraps along it
+                          // (a slab of a decomposed lattice)
     long long N;
     double omega, tau, T0;
     float omega_f, tau_f, T0_f;  // the same, rounded to FP32 on the host (FP32 arithmetic)
@@ -44,6 +47,11 @@ struct StepArgs {
     double mrt_s[2];      // its rates of the third- and fourth-order moments
     float mrt_s_f[2];
 };
+
+// Planes of the march axis a step updates: [halo, np - halo).
+__host__ __device__ __forceinline__ int march_extent(const StepArgs& a, int D) {
+    return (D == 3 ? a.nz : (D == 2 ? a.ny : 1)) - (D >= 2 ? 2 * a.halo : 0);
+}
 
 // Body-force acceleration in the arithmetic type R.
 __host__ __device__ __forceinline__ double acc_param(const StepArgs& a, int c, double) { return a.acc[c]; }

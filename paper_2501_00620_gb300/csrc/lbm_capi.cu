@@ -139,6 +139,7 @@ StepArgs base_args(const lbm_sim* s) {
     a.ny = s->ny;
     a.nz = s->nz;
     a.chunk = s->chunk;
+    a.halo = s->opts.halo;
     a.N = s->N;
     set_step_params(a, s->tau, s->T0);
     a.thermal = s->opts.thermal;
@@ -302,7 +303,7 @@ size_t blocks_of(const lbm_sim* s, int v, int chunk) {
 // Chunk candidates along the march axis: keep at least ~4 waves of blocks on
 // 152 SMs while amortising the two-plane ring of each chunk.
 std::vector<int> chunk_candidates(const lbm_sim* s) {
-    int np = s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1);
+    int np = (s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1)) - (s->D >= 2 ? 2 * s->opts.halo : 0);
     if (s->D == 1) return {1};
     std::vector<int> c;
     for (int k : {8, 10, 12, 14, 16, 20, 24, 28, 32, 64, 128, 256}) {
@@ -644,6 +645,13 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
     if (o.model != LBM_MODEL_BUMP && o.model != LBM_MODEL_STANDARD) return fail(LBM_EINVAL, "unknown model");
     if (o.model == LBM_MODEL_STANDARD && (bc != LBM_BC_PERIODIC || ny > 65535 || nz > 65535))
         return fail(LBM_EINVAL, "the standard comparator runs on periodic lattices with ny, nz <= 65535");
+    if (o.halo != 0 && o.halo != 2) return fail(LBM_EINVAL, "halo must be 0 or 2");
+    if (o.halo) {
+        if (dim < 2 || bc == LBM_BC_WALLS || o.model != LBM_MODEL_BUMP)
+            return fail(LBM_EINVAL, "halo planes: the bump scheme in 2D/3D, periodic or fixed-state in x");
+        if ((dim == 3 ? nz : ny) < 2 * o.halo + 1)
+            return fail(LBM_EINVAL, "halo planes: the slowest axis needs at least one plane besides the halos");
+    }
     long long N = (long long)nx * ny * nz;
     int Q = q_of(dim), NB = nb_of(dim);
     if ((long long)Q * N >= (1LL << 40)) return fail(LBM_EINVAL, "lattice too large");
@@ -1168,6 +1176,143 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     CK(cudaMemset(s->ticket, 0, 64));
     drop_graphs(s);
     return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---- domain decomposition: halo planes of slab simulations -----------------
+
+namespace {
+
+// One stored array of a state buffer as rows of the slowest axis: `rows`
+// rows (planes of populations or of variance components), row pitch and
+// the bytes of one lattice plane within a row.
+struct SlabArrays {
+    size_t f_pitch, f_plane, b_pitch, b_plane;
+    int f_rows, b_rows;
+};
+
+SlabArrays slab_arrays(const lbm_sim* s) {
+    SlabArrays A{};
+    const size_t fb = fbytes_of(s->dtype), rb = rbytes_of(s->dtype);
+    const size_t pstride = s->D == 3 ? (size_t)s->nx * s->ny : (size_t)s->nx;
+    A.f_rows = s->Q;
+    A.f_pitch = (size_t)s->N * fb;
+    A.f_plane = pstride * fb;
+    // variance: component-major planes, or (3D, 32/16-bit storage) three
+    // planes of component pairs interleaved per site
+    const bool paired = s->D == 3 && s->dtype != DT_F64;
+    A.b_rows = paired ? s->NB / 2 : s->NB;
+    A.b_pitch = (size_t)s->N * rb * (paired ? 2 : 1);
+    A.b_plane = pstride * rb * (paired ? 2 : 1);
+    return A;
+}
+
+// Copy `np` planes of the slowest axis starting at plane p_src of sim `a`'s
+// current state into planes starting at p_dst of sim `b`'s current state
+// (populations and variance), on `st`.
+cudaError_t copy_planes(const lbm_sim* a, int p_src, lbm_sim* b, int p_dst, int np, cudaStream_t st) {
+    const SlabArrays A = slab_arrays(a);
+    const char* fs = static_cast<const char*>(a->f[a->cur]);
+    char* fd = static_cast<char*>(b->f[b->cur]);
+    cudaError_t e = cudaMemcpy2DAsync(fd + p_dst * A.f_plane, A.f_pitch, fs + p_src * A.f_plane, A.f_pitch,
+                                      np * A.f_plane, A.f_rows, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return e;
+    const char* bs = static_cast<const char*>(a->b[a->cur]);
+    char* bd = static_cast<char*>(b->b[b->cur]);
+    return cudaMemcpy2DAsync(bd + p_dst * A.b_plane, A.b_pitch, bs + p_src * A.b_plane, A.b_pitch, np * A.b_plane,
+                             A.b_rows, cudaMemcpyDefault, st);
+}
+
+int slab_planes(const lbm_sim* s) { return s->D == 3 ? s->nz : s->ny; }
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_halo_bytes(const lbm_sim* s) {
+    if (!s || !s->opts.halo) return 0;
+    const SlabArrays A = slab_arrays(s);
+    const int h = s->opts.halo;
+    return (size_t)h * (A.f_rows * A.f_plane + A.b_rows * A.b_plane);
+}
+
+lbm_status lbm_halo_pack(lbm_sim* s, int side, void* dst) {
+    if (!s || !dst) return fail(LBM_EINVAL, "NULL argument");
+    if (!s->opts.halo) return fail(LBM_EINVAL, "the simulation has no halo planes (lbm_opts.halo)");
+    if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (low) or 1 (high)");
+    DeviceGuard dg(s->device);
+    const SlabArrays A = slab_arrays(s);
+    const int h = s->opts.halo, n = slab_planes(s);
+    const int p = side == 0 ? h : n - 2 * h;  // the outermost owned planes on that side
+    const char* fs = static_cast<const char*>(s->f[s->cur]);
+    const char* bs = static_cast<const char*>(s->b[s->cur]);
+    char* d = static_cast<char*>(dst);
+    // message: the h planes of every population row, then of every variance row
+    CK(cudaMemcpy2DAsync(d, h * A.f_plane, fs + p * A.f_plane, A.f_pitch, h * A.f_plane, A.f_rows,
+                         cudaMemcpyDefault, s->stream));
+    CK(cudaMemcpy2DAsync(d + (size_t)A.f_rows * h * A.f_plane, h * A.b_plane, bs + p * A.b_plane, A.b_pitch,
+                         h * A.b_plane, A.b_rows, cudaMemcpyDefault, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_unpack(lbm_sim* s, int side, const void* src) {
+    if (!s || !src) return fail(LBM_EINVAL, "NULL argument");
+    if (!s->opts.halo) return fail(LBM_EINVAL, "the simulation has no halo planes (lbm_opts.halo)");
+    if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (low) or 1 (high)");
+    DeviceGuard dg(s->device);
+    const SlabArrays A = slab_arrays(s);
+    const int h = s->opts.halo, n = slab_planes(s);
+    const int p = side == 0 ? 0 : n - h;  // the halo planes on that side
+    char* fd = static_cast<char*>(s->f[s->cur]);
+    char* bd = static_cast<char*>(s->b[s->cur]);
+    const char* m = static_cast<const char*>(src);
+    CK(cudaMemcpy2DAsync(fd + p * A.f_plane, A.f_pitch, m, h * A.f_plane, h * A.f_plane, A.f_rows,
+                         cudaMemcpyDefault, s->stream));
+    CK(cudaMemcpy2DAsync(bd + p * A.b_plane, A.b_pitch, m + (size_t)A.f_rows * h * A.f_plane, h * A.b_plane,
+                         h * A.b_plane, A.b_rows, cudaMemcpyDefault, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_exchange(lbm_sim* const* sims, int k) {
+    if (!sims || k < 1) return fail(LBM_EINVAL, "need at least one slab");
+    for (int i = 0; i < k; ++i) {
+        if (!sims[i]) return fail(LBM_EINVAL, "NULL slab");
+        const lbm_sim* a = sims[i];
+        const lbm_sim* b = sims[0];
+        if (!a->opts.halo) return fail(LBM_EINVAL, "a slab has no halo planes (lbm_opts.halo)");
+        if (a->D != b->D || a->nx != b->nx || (a->D == 3 && a->ny != b->ny) || a->dtype != b->dtype ||
+            a->opts.halo != b->opts.halo)
+            return fail(LBM_EINVAL, "slabs differ in dimension, cross-section, storage or halo depth");
+    }
+    // ordering: every slab's last step is complete (event on its stream)
+    // before any copy out of it; the copies into slab j run on j's stream,
+    // so its next step follows them; and the copies out of slab i finish
+    // before i's step after next, which rewrites that buffer -- i's stream
+    // waits for the other streams' events at the next exchange, and every
+    // step is followed by one
+    std::vector<cudaEvent_t> ev(k);
+    for (int i = 0; i < k; ++i) {
+        DeviceGuard dg(sims[i]->device);
+        CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        CK(cudaEventRecord(ev[i], sims[i]->stream));
+    }
+    lbm_status st = LBM_OK;
+    for (int j = 0; j < k && st == LBM_OK; ++j) {
+        lbm_sim* b = sims[j];
+        DeviceGuard dg(b->device);
+        const int lo = (j + k - 1) % k, hi = (j + 1) % k;
+        const int h = b->opts.halo, nb = slab_planes(b);
+        cudaError_t e = cudaStreamWaitEvent(b->stream, ev[lo], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev[hi], 0);
+        // low halo of j <- the top owned planes of the slab below
+        if (e == cudaSuccess) e = copy_planes(sims[lo], slab_planes(sims[lo]) - 2 * h, b, 0, h, b->stream);
+        // high halo of j <- the bottom owned planes of the slab above
+        if (e == cudaSuccess) e = copy_planes(sims[hi], h, b, nb - h, h, b->stream);
+        if (e != cudaSuccess) st = fail(LBM_ECUDA, std::string("halo exchange: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < k; ++i) cudaEventDestroy(ev[i]);
+    return st;
 }
 
 }  // extern "C"

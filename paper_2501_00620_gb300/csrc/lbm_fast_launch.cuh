@@ -39,7 +39,7 @@ cudaError_t launch_fast(const TmaArgs& ta, cudaStream_t st) {
         attr = true;
     }
     const StepArgs& a = ta.s;
-    const int np = D == 3 ? a.nz : a.ny;
+    const int np = march_extent(a, D);
     dim3 grid(a.nx / TX, D == 3 ? a.ny / TY : 1, (np + a.chunk - 1) / a.chunk);
     kern<<<grid, Sh::NT, Sh::SMEM, st>>>(ta);
     return cudaGetLastError();

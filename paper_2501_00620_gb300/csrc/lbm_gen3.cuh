@@ -27,7 +27,7 @@ cudaError_t gen3_launch_one(const StepArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid = step_grid(3, -1, a.nx, a.ny, a.nz, a.chunk);
+    dim3 grid = step_grid(3, -1, a.nx, a.ny, march_extent(a, 3), a.chunk);
     grid.x = (a.nx + TX - 1) / TX;
     grid.y = (a.ny + TY - 1) / TY;
     kern<<<grid, TX * TY, Sh::smem, st>>>(a);

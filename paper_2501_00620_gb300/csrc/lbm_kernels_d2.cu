@@ -21,7 +21,7 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid = step_grid(kD, -1, a.nx, a.ny, a.nz, a.chunk);
+    dim3 grid = step_grid(kD, -1, a.nx, march_extent(a, kD), a.nz, a.chunk);
     grid.x = (a.nx + TX - 1) / TX;
     if (kD == 3) grid.y = (a.ny + TY - 1) / TY;
     kern<<<grid, TX * TY, Sh::smem, st>>>(a);
@@ -38,7 +38,7 @@ cudaError_t launch_strip_fx(const StepArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((a.nx + Sh::TX - 1) / Sh::TX, 1, (a.ny + a.chunk - 1) / a.chunk);
+    dim3 grid((a.nx + Sh::TX - 1) / Sh::TX, 1, (march_extent(a, 2) + a.chunk - 1) / a.chunk);
     kern<<<grid, kStripNT, Sh::SMEM, st>>>(a);
     return cudaGetLastError();
 }

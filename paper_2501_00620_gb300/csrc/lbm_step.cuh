@@ -87,8 +87,8 @@ __device__ __forceinline__ void step_block(const StepArgs& a, int bx, int by, in
     const int x0 = bx * TX;
     const int y0 = (D == 3) ? by * TY : 0;
     const int np = (D == 3) ? a.nz : (D == 2 ? a.ny : 1);
-    const int p0 = (D == 1) ? 0 : bz * a.chunk;
-    const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np);
+    const int p0 = (D == 1) ? 0 : a.halo + bz * a.chunk;
+    const int p1 = (D == 1) ? 1 : min(p0 + a.chunk, np - a.halo);
     const long long N = a.N;
     real omega, tau, T0;
     step_params(a, omega, tau, T0);

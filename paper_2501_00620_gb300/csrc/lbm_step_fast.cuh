@@ -597,9 +597,10 @@ __global__ void __launch_bounds__(FastShape<D, FS, TX, TY, PFB, MB>::NT, MB)
     int bad = 0;
     uint32_t bphase = 0;
     const int np = (D == 3) ? ta.s.nz : ta.s.ny;
-    const int p0 = blockIdx.z * ta.s.chunk;
+    const int p0 = ta.s.halo + blockIdx.z * ta.s.chunk;
     const bool ok = fast_segment<D, FS, TX, TY, PFB, MB, FX>(ta, smem, blockIdx.x, blockIdx.y, p0,
-                                                             min(p0 + ta.s.chunk, np), acc, bad, bphase, tbase);
+                                                             min(p0 + ta.s.chunk, np - ta.s.halo), acc, bad, bphase,
+                                                             tbase);
     if constexpr (Sh::TM) {
         // every thread's TMEM stores complete, then warp 0 frees the columns
         // (on the abort path too: the segment left with every thread)

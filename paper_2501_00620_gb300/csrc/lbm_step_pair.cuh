@@ -943,9 +943,9 @@ __global__ void __launch_bounds__(PairShape<D, FS, TX, TY, MB, PF>::NT) __maxnre
     PairDiag<D> acc(float(D) * ta.s.T0_f);
     int bad = 0;
     const int np = (D == 3) ? ta.s.nz : ta.s.ny;
-    const int p0 = blockIdx.z * ta.s.chunk;
+    const int p0 = ta.s.halo + blockIdx.z * ta.s.chunk;
     const bool ok = pair_segment<D, FS, TX, TY, MB, PF>(ta, smem, blockIdx.x, blockIdx.y, p0,
-                                                    min(p0 + ta.s.chunk, np), acc, bad, tbase);
+                                                    min(p0 + ta.s.chunk, np - ta.s.halo), acc, bad, tbase);
     // every thread's TMEM stores complete, then warp 0 frees the columns (on
     // the abort path too: the segment left with every thread)
     tmem_wait_st();
@@ -1137,9 +1137,9 @@ __global__ void __launch_bounds__(PairShape<D, FS, TX, TY, 1, 1, true>::NT, 1)
     PairDiag<D> acc(float(D) * ta.s.T0_f);
     int bad = 0;
     const int np = (D == 3) ? ta.s.nz : ta.s.ny;
-    const int p0 = blockIdx.z * ta.s.chunk;
-    const bool ok = pair_segment_ws<D, FS, TX, TY>(ta, smem, blockIdx.x, blockIdx.y, p0, min(p0 + ta.s.chunk, np),
-                                                   acc, bad, tbase);
+    const int p0 = ta.s.halo + blockIdx.z * ta.s.chunk;
+    const bool ok = pair_segment_ws<D, FS, TX, TY>(ta, smem, blockIdx.x, blockIdx.y, p0,
+                                                   min(p0 + ta.s.chunk, np - ta.s.halo), acc, bad, tbase);
     tmem_wait_st();
     tmem_fence_before_sync();
     const bool any_fail = __syncthreads_or(!ok);

@@ -51,7 +51,7 @@ __device__ __forceinline__ void strip_block(const StepArgs& a, int bx, int bz, u
     const int nx = a.nx, np = a.ny, Ni = (int)a.N, rows = (int)a.rows;
     const int x0 = bx * Sh::TX;
     const int txe = min(Sh::TX, nx - x0);  // tile sites of this strip
-    const int p0 = bz * a.chunk, p1 = min(p0 + a.chunk, np);
+    const int p0 = a.halo + bz * a.chunk, p1 = min(p0 + a.chunk, np - a.halo);
     const bool interior = tid >= 1 && tid <= txe;
     const bool active = tid <= txe + 1;
     const int gx = x0 - 1 + tid;

@@ -45,6 +45,7 @@ class lbm_opts(ctypes.Structure):
         ("diagnostics", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("model", ctypes.c_int),
+        ("halo", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,11 @@ def _load():
     L.lbm_set_mrt.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     L.lbm_set_debug.argtypes = [vp, ctypes.c_int]
     L.lbm_set_small_t.argtypes = [vp, ctypes.c_double]
+    L.lbm_halo_bytes.argtypes = [vp]
+    L.lbm_halo_bytes.restype = ctypes.c_size_t
+    L.lbm_halo_pack.argtypes = [vp, ctypes.c_int, vp]
+    L.lbm_halo_unpack.argtypes = [vp, ctypes.c_int, vp]
+    L.lbm_halo_exchange.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     L.lbm_sync.argtypes = [vp]
     L.lbm_moments.argtypes = [vp, ctypes.POINTER(lbm_fields_out)]
     L.lbm_diagnostics.argtypes = [vp, dp]
@@ -150,7 +156,8 @@ def _load():
     L.lbm_server_destroy.restype = None
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_version.restype = ctypes.c_char_p
-    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_set_mrt", "lbm_set_debug", "lbm_set_small_t", "lbm_sync", "lbm_moments",
+    for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_set_force", "lbm_set_wall_velocity", "lbm_set_mrt", "lbm_set_debug", "lbm_set_small_t", "lbm_halo_pack", "lbm_halo_unpack",
+                 "lbm_halo_exchange", "lbm_sync", "lbm_moments",
                  "lbm_diagnostics", "lbm_diagnostics_history", "lbm_last_diagnostics", "lbm_get_state", "lbm_set_state",
                  "lbm_save", "lbm_load", "lbm_step_noalloc", "lbm_launch_config", "lbm_server_create",
                  "lbm_server_submit", "lbm_server_poll", "lbm_server_wait", "lbm_server_stats_get"):
@@ -217,6 +224,23 @@ def lbm_set_small_t(sim, kappa):
 
 def lbm_set_debug(sim, flags):
     _check(_lib.lbm_set_debug(sim, int(flags)))
+
+
+def lbm_halo_bytes(sim):
+    return int(_lib.lbm_halo_bytes(sim))
+
+
+def lbm_halo_pack(sim, side, dst_ptr):
+    _check(_lib.lbm_halo_pack(sim, int(side), ctypes.c_void_p(dst_ptr)))
+
+
+def lbm_halo_unpack(sim, side, src_ptr):
+    _check(_lib.lbm_halo_unpack(sim, int(side), ctypes.c_void_p(src_ptr)))
+
+
+def lbm_halo_exchange(sims):
+    arr = (ctypes.c_void_p * len(sims))(*[s.h if isinstance(s, Simulation) else s for s in sims])
+    _check(_lib.lbm_halo_exchange(arr, len(sims)))
 
 
 def lbm_set_wall_velocity(sim, lo, hi):
@@ -336,7 +360,7 @@ class Simulation:
 
     def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
                  thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
-                 use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump"):
+                 use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump", halo=0):
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -352,6 +376,8 @@ class Simulation:
         o.use_graphs = int(bool(use_graphs))
         o.steps_per_launch = int(steps_per_launch)
         o.model = MODELS[model] if isinstance(model, str) else int(model)
+        o.halo = int(halo)
+        self.halo = int(halo)
         self._allocator = None
         if torch_allocator:
             self._allocator = TorchAllocator(device)
@@ -383,6 +409,18 @@ class Simulation:
     def set_mrt(self, s3, s4):
         """MRT collision (D3Q19): rates of the third- and fourth-order moments."""
         lbm_set_mrt(self.h, s3, s4)
+
+    def halo_bytes(self):
+        """Bytes of one halo message (lbm_opts.halo slabs)."""
+        return lbm_halo_bytes(self.h)
+
+    def halo_pack(self, side, dst_ptr):
+        """Outermost owned planes on `side` (0 low, 1 high) into device memory."""
+        lbm_halo_pack(self.h, side, dst_ptr)
+
+    def halo_unpack(self, side, src_ptr):
+        """A neighbour's message into the halo planes on `side`."""
+        lbm_halo_unpack(self.h, side, src_ptr)
 
     def set_small_t(self, kappa):
         """FP64 temperature recovery where T < kappa |u|^2 (thermal, 32/16-bit storage)."""
