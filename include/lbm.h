@@ -144,6 +144,22 @@ typedef struct {
                                lbm_halo_pack / lbm_halo_unpack after every
                                step).  2D/3D bump scheme, periodic or
                                fixed-state boundary in x */
+    int inplace;            /* 0 (default): A-B buffers of the populations
+                               (one fused pass per step); 1: one population
+                               buffer, updated in place (two passes per step:
+                               pass 1 writes (u0, rho b) per site to an aux
+                               array, pass 2 reads the neighbours' values for
+                               the gradients, collides and writes each site's
+                               new populations into the slots it read; the
+                               slots alternate between the emitted layout
+                               after an even number of steps and the arrived
+                               populations in opposite planes after an odd
+                               one).  Device memory per site: Q + 2 nb +
+                               dim + nb values instead of 2 (Q + nb); HBM
+                               traffic per step about 1.9x the A-B step's.
+                               Bump scheme, periodic boundary, FP64 or FP32
+                               storage; no body force, MRT or small-T
+                               recovery; lbm_save after an even step count */
 } lbm_opts;
 
 typedef struct lbm_sim lbm_sim;

@@ -71,6 +71,7 @@ struct lbm_sim {
     bool mrt = false;  // MRT collision (D3Q19) with rates mrt_s
     int debug = 0;     // LBM_DEBUG_* flags (lbm_set_debug)
     double small_t = 0;  // lbm_set_small_t: FP64 temperature recovery where T < small_t |u|^2
+    void* aux = nullptr;  // opts.inplace: (u0, rho b) planes between the two passes
     double mrt_s[2] = {0, 0};
     lbm_opts opts{};
     int dtype = 0;
@@ -281,7 +282,10 @@ lbm_status tma_maps(lbm_sim* s, int v, int buf, TmaArgs* ta) {
 
 // Launch variant v with arguments a; `buf` is the input buffer (a.fin).
 lbm_status launch_variant(lbm_sim* s, int v, const StepArgs& a, int buf) {
-    if (v == kStdVariant) {
+    if (v == kInplaceVariant) {
+        // the memory form of the population buffer is the parity of the state
+        CK(launch_step_aa(s->D, s->dtype, a, buf, s->aux, s->stream));
+    } else if (v == kStdVariant) {
         CK(launch_std_step(s->D, s->dtype, a, s->stream));
     } else if (v >= kTmaBase) {
         TmaArgs ta;
@@ -296,6 +300,7 @@ lbm_status launch_variant(lbm_sim* s, int v, const StepArgs& a, int buf) {
 }
 
 size_t blocks_of(const lbm_sim* s, int v, int chunk) {
+    if (v == kInplaceVariant) return (size_t)((s->N + 255) / 256);
     dim3 g = step_grid(s->D, v, s->nx, s->ny, s->nz, chunk);
     return (size_t)g.x * g.y * g.z;
 }
@@ -364,7 +369,8 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
 // cooperative launch on scratch copies of the state, and keeps the faster.
 lbm_status tune_multi(lbm_sim* s) {
     s->multi_k = 1;
-    if (s->D != 1 || s->opts.steps_per_launch == 1 || s->opts.model == LBM_MODEL_STANDARD) return LBM_OK;
+    if (s->D != 1 || s->opts.steps_per_launch == 1 || s->opts.model == LBM_MODEL_STANDARD || s->opts.inplace)
+        return LBM_OK;
     if (s->opts.steps_per_launch > 1) {  // forced
         s->multi_k = s->opts.steps_per_launch;
         return LBM_OK;
@@ -452,6 +458,11 @@ lbm_status tune_multi(lbm_sim* s) {
 }
 
 lbm_status autotune(lbm_sim* s) {
+    if (s->opts.inplace) {  // one kernel pair, one thread per site
+        s->var = kInplaceVariant;
+        s->chunk = 0;
+        return ensure_partial(s, s->var, s->chunk);
+    }
     if (s->opts.model == LBM_MODEL_STANDARD) {  // one kernel, planes per block fixed
         s->var = kStdVariant;
         s->chunk = s->opts.chunk > 0 ? s->opts.chunk : 32;
@@ -646,6 +657,10 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
     if (o.model == LBM_MODEL_STANDARD && (bc != LBM_BC_PERIODIC || ny > 65535 || nz > 65535))
         return fail(LBM_EINVAL, "the standard comparator runs on periodic lattices with ny, nz <= 65535");
     if (o.halo != 0 && o.halo != 2) return fail(LBM_EINVAL, "halo must be 0 or 2");
+    if (o.inplace != 0 && o.inplace != 1) return fail(LBM_EINVAL, "inplace must be 0 or 1");
+    if (o.inplace && (bc != LBM_BC_PERIODIC || o.model != LBM_MODEL_BUMP || o.halo ||
+                      (o.dtype != LBM_F64 && o.dtype != LBM_F32)))
+        return fail(LBM_EINVAL, "the in-place step: bump scheme, periodic, FP64 or FP32 storage, no halo");
     if (o.halo) {
         if (dim < 2 || bc == LBM_BC_WALLS || o.model != LBM_MODEL_BUMP)
             return fail(LBM_EINVAL, "halo planes: the bump scheme in 2D/3D, periodic or fixed-state in x");
@@ -686,9 +701,14 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
     size_t fb = fbytes_of(s->dtype), rb = rbytes_of(s->dtype);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
-        s->f[k] = s->dalloc((size_t)Q * N * fb);
+        // in place: one population buffer, both parities refer to it
+        s->f[k] = (o.inplace && k == 1) ? s->f[0] : s->dalloc((size_t)Q * N * fb);
         s->b[k] = s->dalloc((size_t)NB * N * rb);
         ok = s->f[k] && s->b[k];
+    }
+    if (ok && o.inplace) {
+        s->aux = s->dalloc((size_t)(dim + NB) * N * rb);
+        ok = s->aux != nullptr;
     }
     if (ok && bc == LBM_BC_FIXED_STATE) {
         s->gf = s->dalloc((size_t)2 * Q * s->rows * rb);
@@ -771,6 +791,7 @@ lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
 
 lbm_status lbm_set_force(lbm_sim* s, const double* a) {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (s->opts.inplace && a) return fail(LBM_EINVAL, "the in-place step has no body force");
     if (s->opts.model == LBM_MODEL_STANDARD && a) return fail(LBM_EINVAL, "the standard comparator has no body force");
     double v[3] = {0, 0, 0};
     if (a)
@@ -791,6 +812,7 @@ lbm_status lbm_set_force(lbm_sim* s, const double* a) {
 lbm_status lbm_set_mrt(lbm_sim* s, double s3, double s4) {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
     const bool on = s3 > 0 || s4 > 0;
+    if (on && s->opts.inplace) return fail(LBM_EINVAL, "the in-place step runs the SRT collision");
     if (on && (s->D != 3 || s->opts.model != LBM_MODEL_BUMP))
         return fail(LBM_EINVAL, "the MRT collision needs the D3Q19 bump scheme");
     if (on && !(s3 > 0 && s3 < 2 && s4 > 0 && s4 < 2)) return fail(LBM_EINVAL, "MRT rates must lie in (0, 2)");
@@ -806,6 +828,7 @@ lbm_status lbm_set_mrt(lbm_sim* s, double s3, double s4) {
 
 lbm_status lbm_set_small_t(lbm_sim* s, double kappa) {
     if (!s) return fail(LBM_EINVAL, "sim is NULL");
+    if (s->opts.inplace && kappa > 0) return fail(LBM_EINVAL, "the in-place step has no FP64 small-T recovery");
     if (!(kappa >= 0) || !std::isfinite(kappa)) return fail(LBM_EINVAL, "kappa must be finite and >= 0");
     DeviceGuard dg(s->device);
     CK(cudaStreamSynchronize(s->stream));  // graphs captured the old arguments
@@ -1014,6 +1037,11 @@ lbm_status lbm_get_state(lbm_sim* s, double* f, double* b) {
     lbm_status st = LBM_OK;
     cudaError_t e = launch_get_state(s->D, s->dtype, s->f[s->cur], s->b[s->cur], tmp, tmp + (size_t)s->Q * N, N,
                                      s->stream);
+    if (e == cudaSuccess && s->opts.inplace && s->cur == 1) {
+        // in place after an odd number of steps: the arrived populations
+        StepArgs a = base_args(s);
+        e = launch_aa_get_state(s->D, s->dtype, a, tmp, s->stream);
+    }
     if (e == cudaSuccess && f)
         e = cudaMemcpyAsync(f, tmp, (size_t)s->Q * N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess && b)
@@ -1036,6 +1064,12 @@ lbm_status lbm_get_state(lbm_sim* s, double* f, double* b) {
 
 lbm_status lbm_set_state(lbm_sim* s, const double* f, const double* b) {
     if (!s) return fail(LBM_EINVAL, "NULL sim");
+    if (s->opts.inplace && s->cur == 1) {
+        // the buffer holds arrived populations: a full state restarts it in
+        // the emitted layout
+        if (!f || !b) return fail(LBM_EINVAL, "an in-place simulation after an odd step count takes f and b together");
+        s->cur = 0;
+    }
     DeviceGuard dg(s->device);
     const long long N = s->N;
     double* tmp = (double*)s->dalloc((size_t)(s->Q + s->NB) * N * sizeof(double));
@@ -1075,6 +1109,8 @@ struct CkptHeader {
 
 lbm_status lbm_save(lbm_sim* s, const char* path) {
     if (!s || !path) return fail(LBM_EINVAL, "NULL argument");
+    if (s->opts.inplace && s->cur == 1)
+        return fail(LBM_EINVAL, "an in-place simulation is saved after an even number of steps");
     DeviceGuard dg(s->device);
     CK(cudaStreamSynchronize(s->stream));
     const long long N = s->N;
@@ -1158,6 +1194,7 @@ lbm_status lbm_load(lbm_sim* s, const char* path) {
     std::fclose(fp);
     if (!ok) return fail(LBM_EIO, "truncated checkpoint");
     CK(cudaStreamSynchronize(s->stream));
+    if (s->opts.inplace) s->cur = 0;  // the file holds the emitted layout
     CK(cudaMemcpy(s->f[s->cur], buf.data(), fb, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->b[s->cur], buf.data() + fb, bb, cudaMemcpyHostToDevice));
     if (!gbuf.empty()) {

@@ -43,6 +43,7 @@ int n_variants(int D) { return LBM_BY_D(D, n_variants_d1(), n_variants_d2(), n_v
 
 const char* kernel_name(int D, int v) {
     if (v == kStdVariant) return "std_step_kernel";
+    if (v == kInplaceVariant) return "aa_collide_kernel";
     if (v >= kPairBase) return "step_pair_kernel";
     if (v >= kTmaBase) return "step_fast_kernel";
     return (D == 2 && v == 3) ? "step_strip_kernel" : "step_kernel";

@@ -27,6 +27,9 @@ constexpr int kTmaBase = 100;
 // FP32 storage, periodic lattices.
 constexpr int kPairBase = 200;
 
+// Variant index of the in-place two-pass step (lbm_step_aa.cuh).
+constexpr int kInplaceVariant = 900;
+
 // Variant index of the standard-lattice comparator kernel (lbm_std.cu).
 constexpr int kStdVariant = 1000;
 
@@ -65,6 +68,13 @@ cudaError_t launch_get_state(int D, int dtype, const void* f, const void* b, dou
                              long long N, cudaStream_t st);
 cudaError_t launch_set_state(int D, int dtype, void* f, void* b, const double* fi, const double* bi,
                              long long N, cudaStream_t st);
+
+// In-place two-pass step (lbm_kernels_aa.cu): pass 1 (aux) then pass 2 on the
+// population buffer in memory form `form` (0: emitted layout, 1: arrived
+// populations in opposite planes); the emitted state of a form-1 buffer as
+// FP64 population planes.
+cudaError_t launch_step_aa(int D, int dtype, const StepArgs& a, int form, void* aux, cudaStream_t st);
+cudaError_t launch_aa_get_state(int D, int dtype, const StepArgs& a, double* fo, cudaStream_t st);
 
 // Standard-lattice comparator (lbm_std.cu): grid of a step launch, one step,
 // and the start (equilibrium of Eq. 4 for the fields, populations only).

@@ -173,9 +173,16 @@ __device__ __forceinline__ void fd_add(int i, const R* rbn, const R* un, R* F, R
 // second-order Hermite projection whose zeroth, first and second moments are
 // 0, F and G (Eqs. 58-61) -- adds w_i tau (9/2 e_i.G.e_i - 3/2 tr G) to the
 // even part and 3 w_i tau e_i.F to the odd part.
-template <int D, typename FS, typename R, typename I = long long>
+// Where the emitted population i of the site goes: plane i at the site
+// (pull scheme, A-B buffers); the in-place scheme supplies its own map.
+template <typename I> struct PlaneDst {
+    I s;
+    __device__ __forceinline__ I operator()(int i, I N) const { return (I)i * N + s; }
+};
+
+template <int D, typename FS, typename R, typename I = long long, typename Dst = PlaneDst<I>>
 __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R* df, R rho, const R* u,
-                                              const R* F, const R* G, R trG, R omega, R tau) {
+                                              const R* F, const R* G, R trG, R omega, R tau, Dst dst) {
     using L = Lattice<D>;
     constexpr int Q = L::Q, NB = L::NB;
     const R dr = rho - R(1);
@@ -227,7 +234,7 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R*
         ev[0] = dr - dm2 + R(2.0 / 3.0) * F0;
         ev[1] = R(0.5) * dm2 + R(1.0 / 6.0) * (F0 + g45[0]);
     }
-    Store<FS>::st(fo, 0, fma(om1, df[0], omega * ev[0]));
+    Store<FS>::st(fo, dst(0, N), fma(om1, df[0], omega * ev[0]));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int ib = opposite<D>(i);
@@ -238,8 +245,8 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R*
             if (L::e(i, c) != 0) eM += R(L::e(i, c)) * mom[c];
         const R A = omega * ev[i];
         const R B = (R(3.0 * L::w(i)) * omega) * eM;
-        Store<FS>::st(fo, i * N, fma(om1, df[i], A + B));
-        Store<FS>::st(fo, ib * N, fma(om1, df[ib], A - B));
+        Store<FS>::st(fo, dst(i, N), fma(om1, df[i], A + B));
+        Store<FS>::st(fo, dst(ib, N), fma(om1, df[ib], A - B));
     }
 }
 
@@ -280,10 +287,11 @@ __device__ __forceinline__ double temperature64(const float* df, double E64, con
 
 // E64: the site's Ebar summed in FP64 where stage 1 found T small (then T is
 // recovered in FP64 here too); E64 < 0 marks "no FP64 value".
-template <int D, typename FS, typename R, typename I = long long, typename Acc = DiagAcc<R, D + 2>>
+template <int D, typename FS, typename R, typename I = long long, typename Acc = DiagAcc<R, D + 2>,
+          typename Dst = PlaneDst<I>>
 __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_df, const R* c_bt, R rho,
                                              const R* c_j, R c_E, const R* F, const R* G, Acc& acc, int& bad,
-                                             double E64 = -1.0) {
+                                             double E64 = -1.0, Dst dst = Dst{}) {
     using L = Lattice<D>;
     using breal = typename Store<FS>::breal;
     const I N = (I)a.N;
@@ -331,7 +339,10 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_
         a.mout[(1 + D) * N + s] = Tm64;
     }
     if (!a.write_state) return;
-    collide_store<D, FS, R, I>(static_cast<FS*>(a.fout) + s, N, c_df, rho, u, F, G, trG, omega, tau);
+    if constexpr (std::is_same<Dst, PlaneDst<I>>::value)
+        collide_store<D, FS, R, I>(static_cast<FS*>(a.fout), N, c_df, rho, u, F, G, trG, omega, tau, PlaneDst<I>{s});
+    else
+        collide_store<D, FS, R, I>(static_cast<FS*>(a.fout), N, c_df, rho, u, F, G, trG, omega, tau, dst);
     breal* __restrict__ bo = static_cast<breal*>(a.bout);
     R bnew[L::NB];
 #pragma unroll

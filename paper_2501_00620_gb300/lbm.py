@@ -46,6 +46,7 @@ class lbm_opts(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("model", ctypes.c_int),
         ("halo", ctypes.c_int),
+        ("inplace", ctypes.c_int),
     ]
 
 
@@ -360,7 +361,8 @@ class Simulation:
 
     def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
                  thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
-                 use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump", halo=0):
+                 use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump", halo=0,
+                 inplace=False):
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -377,6 +379,7 @@ class Simulation:
         o.steps_per_launch = int(steps_per_launch)
         o.model = MODELS[model] if isinstance(model, str) else int(model)
         o.halo = int(halo)
+        o.inplace = int(bool(inplace))
         self.halo = int(halo)
         self._allocator = None
         if torch_allocator:
