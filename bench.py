@@ -63,6 +63,10 @@ def parse(argv=None):
                    help="grid edge of a smaller instance of the workload (profiling captures); 0: full size")
     p.add_argument("--tile", type=int, default=-1, help="force a kernel tile variant (-1: autotuned)")
     p.add_argument("--chunk", type=int, default=0, help="force planes per block (0: autotuned)")
+    p.add_argument("--steps-per-launch", type=int, default=0,
+                   help="steps per cooperative launch (1D, small 2D; 0: autotuned, 1: single launches)")
+    p.add_argument("--inplace", action="store_true",
+                   help="the in-place step (one population buffer, two passes per step)")
     p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
     p.add_argument("--no-sequential", action="store_true", help="serve: skip the one-at-a-time comparison")
     return p.parse_args(argv)
@@ -162,11 +166,15 @@ def gpu_uuid(dev):
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 
-def algorithmic_bytes_per_site(d, dtype, model="bump"):
+def algorithmic_bytes_per_site(d, dtype, model="bump", inplace=False):
     Q = {1: 3, 2: 9, 3: 19}[d]
     NB = {1: 1, 2: 3, 3: 6}[d] if model == "bump" else 0
     fb = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[dtype]
     bb = 8 if dtype == "f64" else 4
+    if inplace:
+        # two passes: the state is read by both, written once; (u0, rho b)
+        # (d + NB values) is written by the first and read by the second
+        return 3 * (Q * fb + NB * bb) + 2 * (d + NB) * bb
     return 2 * (Q * fb + NB * bb)   # read + write of the emitted state
 
 
@@ -537,7 +545,8 @@ def main():
     stream = torch.cuda.Stream(device=local)
     sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=c["dtype"],
                          thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True,
-                         tile=args.tile, chunk=args.chunk, model=c.get("model", "bump"))
+                         tile=args.tile, chunk=args.chunk, model=c.get("model", "bump"), inplace=args.inplace,
+                         steps_per_launch=args.steps_per_launch)
     sim.init(rho, u, T)
 
     def barrier():
@@ -569,7 +578,8 @@ def main():
     ms_per_step = ms_max / args.steps
 
     # roofline of the step kernel (one launch per step)
-    bps = algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump"))
+    bps = algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump"), args.inplace)
+    launches = args.steps * (2 if args.inplace else 1)
     achieved = N * bps / (ms_per_step * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
     tile, chunk, kernel = sim.launch_config()
@@ -624,16 +634,17 @@ def main():
                    % (N * bps / 2 / 1e9) if N * bps / 2 > 2 * 129e6 else "flush not applied: small lattice",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "kernel": kernel, "tile": tile, "chunk": chunk,
-                   "edge": args.scale or None},
+                   "edge": args.scale or None, "inplace": bool(args.inplace)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "bytes_per_site": bps, "kernel": kernel,
-                     "launches": args.steps,
+                     "launches": launches,
                      "duration": "CUDA events on the launching stream around the timed steps, "
-                                 "one step-kernel launch per step"},
+                                 + ("two launches per step (aux pass, collide pass); bytes of both"
+                                    if args.inplace else "one step-kernel launch per step")},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

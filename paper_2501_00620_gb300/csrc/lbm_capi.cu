@@ -311,6 +311,11 @@ std::vector<int> chunk_candidates(const lbm_sim* s) {
     int np = (s->D == 3 ? s->nz : (s->D == 2 ? s->ny : 1)) - (s->D >= 2 ? 2 * s->opts.halo : 0);
     if (s->D == 1) return {1};
     std::vector<int> c;
+    // lattices of few planes: short marches (more blocks, less latency per step)
+    if (np <= 1024) {
+        c.push_back(2);
+        c.push_back(4);
+    }
     for (int k : {8, 10, 12, 14, 16, 20, 24, 28, 32, 64, 128, 256}) {
         if (k >= np) {
             c.push_back(np);
@@ -342,7 +347,8 @@ lbm_status launch_one_step(lbm_sim* s, bool diag) {
     return LBM_OK;
 }
 
-// K steps of a D1 lattice in one cooperative launch from the current buffer.
+// K steps of a D1 or small D2 lattice in one cooperative launch from the
+// current buffer.
 lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* const* b) {
     StepArgs a[2];
     for (int p = 0; p < 2; ++p) {
@@ -356,7 +362,13 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
         a[p].hist = s->hist;
     }
     const int c = s->cur;
-    cudaError_t e = launch_step_multi_d1(s->dtype, s->var, a[c], a[1 - c], K, s->stream);
+    cudaError_t e;
+    if (s->D == 2) {
+        for (int p = 0; p < 2; ++p) a[p].chunk = kMultiChunk2;
+        e = launch_step_multi_d2(s->dtype, a[c], a[1 - c], K, s->stream);
+    } else {
+        e = launch_step_multi_d1(s->dtype, s->var, a[c], a[1 - c], K, s->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(LBM_ECUDA, std::string("multi-step launch: ") + cudaGetErrorString(e));
@@ -364,13 +376,31 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
     return LBM_OK;
 }
 
-// D1: steps per launch.  opts.steps_per_launch > 1 forces a length; 0 times a
-// replay of 64 single-step launches (CUDA graph) against one 64-step
-// cooperative launch on scratch copies of the state, and keeps the faster.
+// Steps per launch (D1, and D2 lattices of at most kMulti2Sites sites, where a
+// step takes about as long as a launch).  opts.steps_per_launch > 1 forces a
+// length; 0 times a replay of 64 single-step launches (CUDA graph) against
+// one 64-step cooperative launch on scratch copies of the state, and keeps
+// the faster.
+constexpr long long kMulti2Sites = 1LL << 18;
 lbm_status tune_multi(lbm_sim* s) {
     s->multi_k = 1;
-    if (s->D != 1 || s->opts.steps_per_launch == 1 || s->opts.model == LBM_MODEL_STANDARD || s->opts.inplace)
+    // D2: only for autotuned tiles (a forced tile runs as asked) or when the
+    // caller asks for a length
+    const bool small2 = s->D == 2 && s->N <= kMulti2Sites && !s->opts.halo &&
+                        (s->opts.tile < 0 || s->opts.steps_per_launch > 1);
+    if ((s->D != 1 && !small2) || s->opts.steps_per_launch == 1 || s->opts.model == LBM_MODEL_STANDARD ||
+        s->opts.inplace)
         return LBM_OK;
+    if (s->D == 2) {
+        // the cooperative D2 launch has a fixed tiling: diagnostics partials for it
+        const size_t nb = (size_t)((s->nx + kMultiTX2 - 1) / kMultiTX2) * ((s->ny + kMultiChunk2 - 1) / kMultiChunk2);
+        if (nb > s->partial_blocks) {
+            double* p = (double*)s->dalloc(nb * (s->D + 2) * sizeof(double));
+            if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");
+            s->partial = p;
+            s->partial_blocks = nb;
+        }
+    }
     if (s->opts.steps_per_launch > 1) {  // forced
         s->multi_k = s->opts.steps_per_launch;
         return LBM_OK;
@@ -421,6 +451,11 @@ lbm_status tune_multi(lbm_sim* s) {
             // single steps on the same scratch buffers, captured as one graph
             void* sf[2] = {s->f[0], s->f[1]};
             void* sb[2] = {s->b[0], s->b[1]};
+            // the staged kernels' tensor maps are cached per variant with the
+            // buffers they were built for: keep the real buffers' maps aside,
+            // and drop every map built for the scratch buffers afterwards
+            auto saved_maps = s->tmaps;
+            s->tmaps.clear();
             s->f[0] = tf[0], s->f[1] = tf[1], s->b[0] = tb[0], s->b[1] = tb[1];
             cudaGraphExec_t ge = nullptr;
             cudaGraph_t g;
@@ -441,6 +476,8 @@ lbm_status tune_multi(lbm_sim* s) {
             }
             cudaGetLastError();
             s->f[0] = sf[0], s->f[1] = sf[1], s->b[0] = sb[0], s->b[1] = sb[1];
+            cudaStreamSynchronize(s->stream);  // the scratch runs are done before their maps go
+            s->tmaps = saved_maps;
             // launch_one_step flipped s->cur K times: K is even
         }
     }

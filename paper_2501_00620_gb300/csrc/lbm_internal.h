@@ -60,6 +60,11 @@ cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t
 cudaError_t launch_step_multi_d1(int dtype, int v, const StepArgs& a0, const StepArgs& a1, int K,
                                  cudaStream_t st);
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st);
+// K steps of a small D2 lattice in one cooperative launch (the generic
+// kernel's strips of kMultiTX2 sites, a0.chunk rows per block).
+constexpr int kMultiTX2 = 128;
+constexpr int kMultiChunk2 = 8;
+cudaError_t launch_step_multi_d2(int dtype, const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st);
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
                         void* b, long long N, cudaStream_t st);
 cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,

@@ -89,6 +89,35 @@ cudaError_t by_dtype(int dtype, F&& f) {
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
+// K steps of a small D2 lattice in one cooperative launch: the generic
+// kernel's strips of kMultiTX2 sites (a.chunk rows each) meet at a grid-wide
+// barrier after every step.  cudaErrorCooperativeLaunchTooLarge if the grid
+// cannot be resident at once.
+template <typename FS>
+cudaError_t launch_multi_d2_fs(const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st) {
+    constexpr int TX = kMultiTX2;
+    using Sh = StepShape<kD, FS, TX, 1>;
+    auto kern = step_multi_kernel<kD, FS, TX, 1>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((a0.nx + TX - 1) / TX, 1, (march_extent(a0, kD) + a0.chunk - 1) / a0.chunk);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX, Sh::smem);
+    if (e != cudaSuccess) return e;
+    if ((long long)per_sm * device_sms() < (long long)grid.x * grid.z) return cudaErrorCooperativeLaunchTooLarge;
+    StepArgs p0 = a0, p1 = a1;
+    void* args[] = {&p0, &p1, &K};
+    return cudaLaunchCooperativeKernel((const void*)kern, grid, dim3(TX), args, Sh::smem, st);
+}
+
+cudaError_t launch_step_multi_d2(int dtype, const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st) {
+    return by_dtype(dtype, [&](auto tag) { return launch_multi_d2_fs<decltype(tag)>(a0, a1, K, st); });
+}
+
 cudaError_t launch_step_d2(int dtype, int v, const StepArgs& a, cudaStream_t st) {
     return by_dtype(dtype, [&](auto tag) { return launch_dtype<decltype(tag)>(v, a, st); });
 }

@@ -581,6 +581,42 @@ def test_small_t_fp64_recovery(d):
     g.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_2d_multi_step_launch_equals_single_steps(dtype):
+    """Small D2 lattices may run many steps per cooperative launch (the
+    generic kernel's 128-site strips with a grid-wide barrier between
+    steps): the same bits as single launches of the same tile in FP64 (FP32:
+    the two kernels are compiled apart and may contract multiply-adds
+    differently, so within FP32 rounding), and the per-step diagnostics
+    history is recorded for every step."""
+    shape = (1, 64, 96)
+    rng = np.random.default_rng(37)
+    rho = 1 + 0.05 * rng.random(shape)
+    u = 0.03 * rng.standard_normal((2,) + shape)
+    T = 0.1 * (1 + 0.05 * rng.random(shape))
+    m = lbm.Simulation(2, 96, 64, 1, tau=0.6, T0=0.1, thermal=True, dtype=dtype, steps_per_launch=16)
+    r = lbm.Simulation(2, 96, 64, 1, tau=0.6, T0=0.1, thermal=True, dtype=dtype, tile=1, chunk=4,
+                       steps_per_launch=1)
+    for s in (m, r):
+        s.init(rho, u, T)
+        s.step(48)
+    assert m.launch_config()[2] == "step_multi_kernel"
+    fm, bm = m.emitted()
+    fr, br = r.emitted()
+    if dtype == "f64":
+        assert np.array_equal(fm, fr) and np.array_equal(bm, br)
+    else:
+        assert normwise(fm, fr) < 2e-6 and np.abs(bm - br).max() < 2e-6
+    h = m.diagnostics_history()
+    assert len(h) == 48 and h[-1, 0] == 47
+    # momentum and energy as fractions of the mass (FP32: the per-site
+    # gradient terms round differently in the two compilations)
+    np.testing.assert_allclose(h, r.diagnostics_history(), rtol=1e-12 if dtype == "f64" else 1e-9,
+                               atol=(1e-12 if dtype == "f64" else 1e-9) * h[0, 1])
+    m.close()
+    r.close()
+
+
 STRIP_TILE = 3
 
 
