@@ -17,8 +17,9 @@ struct PairVariant {
 // 64 x 8 at one block per SM (more registers per thread, a smaller ring);
 // 64 x 8 warp-specialized (mb = 0), one block per SM.
 constexpr PairVariant kPair3[] = {{64, 4, 2, 0}, {64, 8, 1, 1}, {64, 8, 0, 1}};
-// D2Q9: strips of 128 sites (64 pairs) at four blocks per SM.
-constexpr PairVariant kPair2[] = {{128, 1, 4, 1}};
+// D2Q9: strips of 128 sites (64 pairs) at four, six and eight blocks per SM
+// (the register budget per thread falls as the blocks per SM grow).
+constexpr PairVariant kPair2[] = {{128, 1, 4, 1}, {128, 1, 6, 1}, {128, 1, 8, 1}};
 
 // MB = 0 selects the warp-specialized form (one block per SM).
 template <int D, typename FS, int TX, int TY, int MB, int PF>
@@ -73,6 +74,8 @@ cudaError_t pair_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t 
     } else {
         switch (k) {
             LBM_PAIR_CASE(2, kPair2, 0)
+            LBM_PAIR_CASE(2, kPair2, 1)
+            LBM_PAIR_CASE(2, kPair2, 2)
             default: return cudaErrorInvalidValue;
         }
     }

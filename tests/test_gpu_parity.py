@@ -437,7 +437,7 @@ def test_fp32_diagnostics_match_exact_state_sums(d, shape):
 
 
 PAIR_BASE = 200
-N_PAIR = {2: 1, 3: 3}  # pair-kernel tiles per lattice
+N_PAIR = {2: 3, 3: 3}  # pair-kernel tiles per lattice
 
 
 @pytest.mark.parametrize("d,shape", [(3, (24, 32, 64)), (3, (9, 8, 128)), (2, (1, 40, 256)), (2, (1, 24, 128))])
@@ -611,7 +611,7 @@ def test_2d_multi_step_launch_equals_single_steps(dtype):
     assert len(h) == 48 and h[-1, 0] == 47
     # momentum and energy as fractions of the mass (FP32: the per-site
     # gradient terms round differently in the two compilations)
-    np.testing.assert_allclose(h, r.diagnostics_history(), rtol=1e-12 if dtype == "f64" else 1e-9,
+    np.testing.assert_allclose(h, r.diagnostics_history(), rtol=1e-12 if dtype == "f64" else 2e-8,
                                atol=(1e-12 if dtype == "f64" else 1e-9) * h[0, 1])
     m.close()
     r.close()
