@@ -579,6 +579,9 @@ def main():
 
     # roofline of the step kernel (one launch per step)
     bps = algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump"), args.inplace)
+    # one buffer of the emitted state (the A-B form; the in-place form keeps
+    # one population buffer and two variance buffers)
+    state_b = N * algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump")) / 2
     launches = args.steps * (2 if args.inplace else 1)
     achieved = N * bps / (ms_per_step * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
@@ -630,8 +633,8 @@ def main():
         "vs_baseline": None, "dtype": "f64" if c["dtype"] == "f64" else "f32",
         "data": "synthetic",
         "config": {"workload": name + ": " + WORKLOAD_TEXT[name], "storage": c["dtype"],
-                   "sites": N, "l2": "state of %.2f GB per buffer > 129 MB L2, no flush needed"
-                   % (N * bps / 2 / 1e9) if N * bps / 2 > 2 * 129e6 else "flush not applied: small lattice",
+                   "sites": N, "l2": ("state of %.3f GB per buffer > 129 MB L2, no flush needed" % (state_b / 1e9))
+                   if state_b > 129e6 else "flush not applied: state of %.1f MB per buffer fits in L2" % (state_b / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "kernel": kernel, "tile": tile, "chunk": chunk,
                    "edge": args.scale or None, "inplace": bool(args.inplace)},

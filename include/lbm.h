@@ -121,12 +121,16 @@ typedef struct {
     void *alloc_ctx;
     int tile;               /* kernel variant index; -1 (default): autotuned */
     int chunk;              /* planes per block along the march axis; 0: auto */
-    int steps_per_launch;   /* 1D lattices: steps per cooperative launch (a
-                               grid-wide barrier between steps, the same bits
-                               as single steps); 0 (default): the faster of
-                               64 per launch and CUDA-graph replays of single
-                               steps, timed at the first lbm_step on scratch
-                               copies of the state; 1: single steps */
+    int steps_per_launch;   /* 1D lattices, and 2D lattices of at most 2^18
+                               sites without halo: steps per cooperative
+                               launch (a grid-wide barrier between steps; 1D
+                               and FP64 2D give the same bits as single steps,
+                               FP32 2D the same up to FP32 rounding); 0
+                               (default): the faster of 64 per launch and
+                               CUDA-graph replays of single steps, timed at
+                               the first lbm_step on scratch copies of the
+                               state (2D: only with an autotuned tile); 1:
+                               single steps */
     int diagnostics;        /* 1 (default): every step also reduces mass,
                                momentum and energy of the state it consumes
                                into a device history (lbm_diagnostics_history);

@@ -207,12 +207,13 @@ struct Request {
 };
 
 // Precision policy: FP32 storage and arithmetic, except 1D fixed-state
-// (Riemann) requests, which run in FP64.  In FP32 the two-state problem of
-// BASELINE config 2 leaves the physical range (rho <= 0) after about 1600
-// steps -- rounding-size perturbations at the front grow until they are
-// O(1) -- and requests ask for up to 5000 steps; from FP64 rounding the same
-// growth stays small over that span (every 1D Riemann request of the
-// seeded serving mix stays finite with rho > 0 in the FP64 oracle).  1D
+// (Riemann) requests, which run in FP64.  In FP32 the 4096-cell two-state
+// problem leaves the physical range (rho <= 0) after about 1600 steps --
+// rounding-size perturbations at the front grow until they are O(1) -- and
+// requests ask for up to 5000 steps; from FP64 rounding the same growth
+// takes about three times as many steps, so FP64 carries most of them.  (On
+// the longest runs over the longest lattices the scheme leaves the physical
+// range in the FP64 oracle too; the server reports those as unstable.)  1D
 // lattices are a small share of the work of a mix.
 int request_dtype(int d, lbm_bc bc) { return (d == 1 && bc == LBM_BC_FIXED_STATE) ? DT_F64 : DT_F32; }
 

@@ -1,5 +1,5 @@
 """Writes riemann_mix_oracle.txt: for every 1D two-state Riemann request of
-the seeded serving mix (BASELINE config 5, seed 0, 1000 requests), whether
+the seeded serving mix (seed 0, 1000 requests), whether
 the FP64 oracle's state after the requested steps is non-physical (rho <= 0
 or not finite) -- the requests on which the scheme itself, at the mix's
 Riemann parameters (tau 0.55, T unit 0.15, fixed-state reservoirs), leaves

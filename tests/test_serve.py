@@ -121,7 +121,7 @@ def test_matches_oracle_sound_wave():
 
 
 def _long_riemann_requests():
-    """1D Riemann requests of the seeded serving mix (BASELINE config 5): the
+    """1D Riemann requests of the seeded serving mix (1000 requests): the
     three with the most steps among lattices of at most 2048 sites, and the
     two with the most steps per site (the shock reflects from the frozen
     reservoirs many times) -- the requests that left the physical range
