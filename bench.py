@@ -39,6 +39,11 @@ WORKLOAD_TEXT = {
              "T0=0.1; tau=0.6; thermal",
     "std3d": "standard-lattice comparator (BGK, Hermite equilibrium of Eq. 4) on D3Q19 256^3 periodic; "
              "the turb3d velocity field (Mach 0.12 at cs2 = 1/3); T0=1/3; tau=0.52",
+    "channel3d": "D3Q19 256^3 plane Poiseuille channel: half-way bounce-back walls normal to z, uniform "
+                 "acceleration 1e-7 along x, from rest (rho=1, u=0, T=T0=0.1); tau=0.6; isothermal; "
+                 "generic kernel (walls and force)",
+    "mrt3d": "the turb3d lattice and fields with the MRT collision of Appendix B (s3=1.2, s4=1.4); "
+             "generic kernel",
     "sound1d": "D1Q3 256 periodic sound wave, rho=1+1e-3 sin(2 pi x/256), T0=1/3, tau=0.8; isothermal",
     "riemann1d": "D1Q3 4096 two-state Riemann (rho 1:0.125, T 1.0:0.8 x 0.15), tau=0.55; thermal; "
                  "fixed-state ends",
@@ -65,6 +70,10 @@ def parse(argv=None):
     p.add_argument("--chunk", type=int, default=0, help="force planes per block (0: autotuned)")
     p.add_argument("--steps-per-launch", type=int, default=0,
                    help="steps per cooperative launch (1D, small 2D; 0: autotuned, 1: single launches)")
+    p.add_argument("--cluster", type=int, default=0,
+                   help="small periodic 2D lattices: cluster-resident kernel (-1 never, 0 autotuned, 1+v variant v)")
+    p.add_argument("--no-diagnostics", action="store_true",
+                   help="steps without the per-step conservation sums (lbm_opts.diagnostics = 0)")
     p.add_argument("--inplace", action="store_true",
                    help="the in-place step (one population buffer, two passes per step)")
     p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
@@ -265,6 +274,15 @@ def workload_params(name, dtype_override):
     return c
 
 
+def apply_settings(sim, c):
+    """Body force and MRT rates of a workload, on the library's Simulation or
+    the oracle's (the two share these method names)."""
+    if c.get("force"):
+        sim.set_force(list(c["force"]))
+    if c.get("mrt"):
+        sim.set_mrt(*c["mrt"])
+
+
 def oracle_sample(name, budget_s, steps_total):
     """A bounded sample of the workload for the CPU oracle: a smaller lattice
     of the same generator, sized so that steps_total steps take ~budget_s."""
@@ -284,6 +302,7 @@ def oracle_sample(name, budget_s, steps_total):
     s = oracle.Sim(d, n_probe, n_probe if d >= 2 else 1, n_probe if d == 3 else 1, tau=c["tau"], T0=c["T0"],
                    thermal=c["thermal"], bc=c["bc"], model=c.get("model", "bump"))
     s.init(rho, u, T)
+    apply_settings(s, c)
     t0 = time.perf_counter()
     s.step(2)
     rate = 2 * sites_probe / (time.perf_counter() - t0)
@@ -305,6 +324,7 @@ def run_oracle(name, n, steps, warmup):
     s = oracle.Sim(d, n, n if d >= 2 else 1, n if d == 3 else 1, tau=c["tau"], T0=c["T0"],
                    thermal=c["thermal"], bc=c["bc"], model=c.get("model", "bump"))
     s.init(rho, u, T)
+    apply_settings(s, c)
     s.step(warmup)
     t0 = time.perf_counter()
     s.step(steps)
@@ -544,10 +564,12 @@ def main():
 
     stream = torch.cuda.Stream(device=local)
     sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=c["dtype"],
-                         thermal=c["thermal"], device=local, stream=stream.cuda_stream, diagnostics=True,
+                         thermal=c["thermal"], device=local, stream=stream.cuda_stream,
+                         diagnostics=not args.no_diagnostics,
                          tile=args.tile, chunk=args.chunk, model=c.get("model", "bump"), inplace=args.inplace,
-                         steps_per_launch=args.steps_per_launch)
+                         steps_per_launch=args.steps_per_launch, cluster=args.cluster)
     sim.init(rho, u, T)
+    apply_settings(sim, c)
 
     def barrier():
         if dist is not None:
@@ -582,15 +604,18 @@ def main():
     # one buffer of the emitted state (the A-B form; the in-place form keeps
     # one population buffer and two variance buffers)
     state_b = N * algorithmic_bytes_per_site(d, c["dtype"], c.get("model", "bump")) / 2
-    launches = args.steps * (2 if args.inplace else 1)
+    tile, chunk, kernel = sim.launch_config()
+    if kernel in ("step_multi_kernel", "step_cluster_kernel"):
+        launches = -(-args.steps // chunk)  # chunk = steps per launch
+    else:
+        launches = args.steps * (2 if args.inplace else 1)
     achieved = N * bps / (ms_per_step * 1e-3) / 1e9
     peak, peak_src = hbm_peak()
-    tile, chunk, kernel = sim.launch_config()
     traffic = profiled_traffic(kernel, name, c["dtype"])
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.no_diagnostics:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hr, hu, hT = pin(rho), pin(u), pin(T)
         orr = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
@@ -637,7 +662,8 @@ def main():
                    if state_b > 129e6 else "flush not applied: state of %.1f MB per buffer fits in L2" % (state_b / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "kernel": kernel, "tile": tile, "chunk": chunk,
-                   "edge": args.scale or None, "inplace": bool(args.inplace)},
+                   "edge": args.scale or None, "inplace": bool(args.inplace),
+                   "diagnostics": not args.no_diagnostics},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src, "bytes_per_site": bps, "kernel": kernel,

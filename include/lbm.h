@@ -164,6 +164,23 @@ typedef struct {
                                Bump scheme, periodic boundary, FP64 or FP32
                                storage; no body force, MRT or small-T
                                recovery; lbm_save after an even step count */
+    int cluster;            /* multi-step launches of small periodic 2D
+                               lattices with the whole state resident in the
+                               shared memory of one thread-block cluster (up
+                               to 16 blocks on 16 multiprocessors, neighbour
+                               rows read through distributed shared memory;
+                               FP32 or FP64 storage, bump scheme, no walls,
+                               force, MRT or small-T recovery, no halo): 0
+                               (default) the steps-per-launch autotuner
+                               times it with the other forms; -1 never; 1 + v
+                               forces cluster variant v (0: 16 blocks of 256
+                               threads, 1: 16 x 512, 2: 8 x 512) with
+                               steps_per_launch steps per launch (64 if not
+                               > 1); lbm_step then fails with LBM_EINVAL if
+                               the lattice does not fit that variant.  A
+                               setting only the generic kernel has (body
+                               force, MRT, small-T recovery) takes
+                               precedence over a forced variant */
 } lbm_opts;
 
 typedef struct lbm_sim lbm_sim;
@@ -304,10 +321,12 @@ long lbm_step_count(const lbm_sim *sim);
 /* The launch configuration of the step (library service, no counterpart in
  * the paper): *tile = the tile variant in use (0.. the generic fused kernel;
  * on D2Q9 3 = the strip kernel; 100.. the shared-memory-staged kernels;
- * *kernel = "step_multi_kernel" when 1D steps run several per cooperative
- * launch), *chunk = planes per thread block
- * along the slowest axis, *kernel = name of the kernel template (static
- * string).  Fixed by opts.tile/opts.chunk or by the autotuner at the first
+ * 200.. the pair kernel; 300 + v the cluster-resident kernel's variant v;
+ * 900 the in-place step), *chunk = planes per thread block along the slowest
+ * axis, or steps per launch when several steps run per launch, *kernel =
+ * name of the kernel template (static string; "step_multi_kernel" or
+ * "step_cluster_kernel" when several steps run per launch).  Fixed by
+ * opts.tile/opts.chunk/opts.cluster or by the autotuner at the first
  * lbm_step; before that *tile = *chunk = -1 and *kernel = "".  Any pointer
  * may be NULL.  Host only, never fails for a valid handle. */
 lbm_status lbm_launch_config(const lbm_sim *sim, int *tile, int *chunk, const char **kernel);

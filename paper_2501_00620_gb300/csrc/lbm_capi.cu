@@ -93,7 +93,8 @@ struct lbm_sim {
     double* diag_out = nullptr;
     double* fields = nullptr;  // (D+2) N doubles: init input / moments output
     int var = -1, chunk = 0;
-    int multi_k = 0;  // D1: steps per cooperative launch (0: not decided, 1: single steps)
+    int multi_k = 0;  // steps per multi-step launch (0: not decided, 1: single steps)
+    int cluster_v = -1;  // >= 0: the multi-step launches run the cluster-resident kernel, variant cluster_v
     long nstep = 0;
     // graphs: [parity of cur] -> executable graph of kGraphSteps launches
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -363,7 +364,9 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
     }
     const int c = s->cur;
     cudaError_t e;
-    if (s->D == 2) {
+    if (s->D == 2 && s->cluster_v >= 0) {
+        e = launch_step_cluster_d2(s->dtype, s->cluster_v, a[c], a[1 - c], K, s->stream);
+    } else if (s->D == 2) {
         for (int p = 0; p < 2; ++p) a[p].chunk = kMultiChunk2;
         e = launch_step_multi_d2(s->dtype, a[c], a[1 - c], K, s->stream);
     } else {
@@ -379,11 +382,59 @@ lbm_status launch_multi(lbm_sim* s, int K, bool diag, void* const* f, void* cons
 // Steps per launch (D1, and D2 lattices of at most kMulti2Sites sites, where a
 // step takes about as long as a launch).  opts.steps_per_launch > 1 forces a
 // length; 0 times a replay of 64 single-step launches (CUDA graph) against
-// one 64-step cooperative launch on scratch copies of the state, and keeps
-// the faster.
+// one 64-step cooperative launch and, for periodic D2 lattices that fit the
+// shared memory of a thread-block cluster, against 64 steps of each cluster
+// variant, on scratch copies of the state, and keeps the fastest.
 constexpr long long kMulti2Sites = 1LL << 18;
+
+// The cluster-resident kernel serves periodic D2 bump lattices in FP32/FP64
+// without the generic kernel's settings (walls, force, MRT, small-T).
+bool cluster_applicable(const lbm_sim* s, int v) {
+    return s->D == 2 && s->bc == LBM_BC_PERIODIC && s->opts.model != LBM_MODEL_STANDARD && !s->opts.inplace &&
+           !s->opts.halo && !generic_only(s) && (s->dtype == DT_F32 || s->dtype == DT_F64) &&
+           cluster_fits_d2(s->dtype, v, s->nx, s->ny) &&
+           launch_step_cluster_d2(s->dtype, v, base_args(s), base_args(s), 1, s->stream, true) == cudaSuccess;
+}
+
+// Shortest of three timed runs of `run` (CUDA events on stream st); 1e30 if
+// the events fail.
+template <typename F> float best_of(cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, F run) {
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        float t = 1e30f;
+        cudaEventRecord(e0, st);
+        run();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && t < best)
+            best = t;
+    }
+    return best;
+}
+
 lbm_status tune_multi(lbm_sim* s) {
     s->multi_k = 1;
+    s->cluster_v = -1;
+    cudaGetLastError();
+    // forced cluster variant (opts.cluster = 1 + v); a setting only the
+    // generic kernel has (force, MRT, small-T) takes precedence
+    if (s->opts.cluster > 0 && !generic_only(s)) {
+        const int v = s->opts.cluster - 1;
+        if (!cluster_applicable(s, v)) {
+            cudaGetLastError();
+            return fail(LBM_EINVAL, "opts.cluster: the lattice does not fit that cluster variant "
+                                    "(periodic D2 bump lattice, FP32/FP64, no halo, rows >= blocks, "
+                                    "state within the cluster's shared memory)");
+        }
+        if ((size_t)cluster_blocks(v) > s->partial_blocks) {
+            double* p = (double*)s->dalloc((size_t)cluster_blocks(v) * (s->D + 2) * sizeof(double));
+            if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");
+            s->partial = p;
+            s->partial_blocks = cluster_blocks(v);
+        }
+        s->cluster_v = v;
+        s->multi_k = s->opts.steps_per_launch > 1 ? s->opts.steps_per_launch : 64;
+        return LBM_OK;
+    }
     // D2: only for autotuned tiles (a forced tile runs as asked) or when the
     // caller asks for a length
     const bool small2 = s->D == 2 && s->N <= kMulti2Sites && !s->opts.halo &&
@@ -440,12 +491,8 @@ lbm_status tune_multi(lbm_sim* s) {
         }
         // the timing runs write a scratch flag word only if the state is bad;
         // diagnostics off, the history untouched
-        if (launch_multi(s, K, false, tf, tb) == LBM_OK) {
-            cudaEventRecord(e0, s->stream);
-            launch_multi(s, K, false, tf, tb);
-            cudaEventRecord(e1, s->stream);
-            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t_multi, e0, e1);
-        }
+        if (launch_multi(s, K, false, tf, tb) == LBM_OK)
+            t_multi = best_of(e0, e1, s->stream, [&] { launch_multi(s, K, false, tf, tb); });
         cudaGetLastError();
         {
             // single steps on the same scratch buffers, captured as one graph
@@ -465,10 +512,7 @@ lbm_status tune_multi(lbm_sim* s) {
                 if (cudaStreamEndCapture(s->stream, &g) == cudaSuccess) {
                     if (st == LBM_OK && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
                         cudaGraphLaunch(ge, s->stream);
-                        cudaEventRecord(e0, s->stream);
-                        cudaGraphLaunch(ge, s->stream);
-                        cudaEventRecord(e1, s->stream);
-                        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t_graph, e0, e1);
+                        t_graph = best_of(e0, e1, s->stream, [&] { cudaGraphLaunch(ge, s->stream); });
                         cudaGraphExecDestroy(ge);
                     }
                     cudaGraphDestroy(g);
@@ -481,6 +525,27 @@ lbm_status tune_multi(lbm_sim* s) {
             // launch_one_step flipped s->cur K times: K is even
         }
     }
+    // the cluster-resident kernel (periodic D2 lattices that fit), each variant
+    float t_cluster = 1e30f;
+    int best_cluster = -1;
+    if (ok && s->D == 2 && s->opts.cluster == 0) {
+        for (int v = 0; v < n_cluster_variants(); ++v) {
+            if (!cluster_applicable(s, v)) {
+                cudaGetLastError();
+                continue;
+            }
+            s->cluster_v = v;
+            float t = 1e30f;
+            if (launch_multi(s, K, false, tf, tb) == LBM_OK)
+                t = best_of(e0, e1, s->stream, [&] { launch_multi(s, K, false, tf, tb); });
+            cudaGetLastError();
+            s->cluster_v = -1;
+            if (t < t_cluster) {
+                t_cluster = t;
+                best_cluster = v;
+            }
+        }
+    }
     cudaStreamSynchronize(s->stream);
     if (ok) cudaMemcpy(s->flag, &flag0, sizeof(int), cudaMemcpyHostToDevice);
     if (e0) cudaEventDestroy(e0);
@@ -490,7 +555,18 @@ lbm_status tune_multi(lbm_sim* s) {
         tmp_free(tb[k], bb);
     }
     cudaGetLastError();
-    if (t_multi < t_graph) s->multi_k = K;
+    if (best_cluster >= 0 && t_cluster < t_graph && t_cluster < t_multi) {
+        if ((size_t)cluster_blocks(best_cluster) > s->partial_blocks) {
+            double* p = (double*)s->dalloc((size_t)cluster_blocks(best_cluster) * (s->D + 2) * sizeof(double));
+            if (!p) return fail(LBM_ENOMEM, "diagnostics partial buffer");
+            s->partial = p;
+            s->partial_blocks = cluster_blocks(best_cluster);
+        }
+        s->cluster_v = best_cluster;
+        s->multi_k = K;
+    } else if (t_multi < t_graph) {
+        s->multi_k = K;
+    }
     return LBM_OK;
 }
 
@@ -617,9 +693,10 @@ void drop_graphs(lbm_sim* s) {
 // A setting only the generic kernel implements (walls, force, MRT) sends a
 // lattice tuned onto another kernel back to the autotuner.
 void retune_if_needed(lbm_sim* s) {
-    if (s->var >= 0 && !variant_allowed(s, s->var)) {
+    if ((s->var >= 0 && !variant_allowed(s, s->var)) || (s->cluster_v >= 0 && generic_only(s))) {
         s->var = -1;
         s->multi_k = 0;
+        s->cluster_v = -1;
     }
 }
 
@@ -695,6 +772,8 @@ lbm_status lbm_create_ex(int dim, int nx, int ny, int nz, double tau, double T0,
         return fail(LBM_EINVAL, "the standard comparator runs on periodic lattices with ny, nz <= 65535");
     if (o.halo != 0 && o.halo != 2) return fail(LBM_EINVAL, "halo must be 0 or 2");
     if (o.inplace != 0 && o.inplace != 1) return fail(LBM_EINVAL, "inplace must be 0 or 1");
+    if (o.cluster < -1 || o.cluster > n_cluster_variants())
+        return fail(LBM_EINVAL, "cluster must be -1, 0 or 1 + a cluster variant");
     if (o.inplace && (bc != LBM_BC_PERIODIC || o.model != LBM_MODEL_BUMP || o.halo ||
                       (o.dtype != LBM_F64 && o.dtype != LBM_F32)))
         return fail(LBM_EINVAL, "the in-place step: bump scheme, periodic, FP64 or FP32 storage, no halo");
@@ -975,10 +1054,13 @@ long lbm_step_count(const lbm_sim* s) { return s ? s->nstep : -1; }
 
 lbm_status lbm_launch_config(const lbm_sim* s, int* tile, int* chunk, const char** kernel) {
     if (!s) return fail(LBM_EINVAL, "NULL simulation");
-    if (tile) *tile = s->var;
-    if (chunk) *chunk = s->var >= 0 ? s->chunk : -1;
+    const bool cl = s->multi_k > 1 && s->cluster_v >= 0;
+    if (tile) *tile = cl ? kClusterBase + s->cluster_v : s->var;
+    if (chunk) *chunk = s->var >= 0 ? (s->multi_k > 1 ? s->multi_k : s->chunk) : -1;
     if (kernel)
-        *kernel = s->var < 0 ? "" : (s->multi_k > 1 ? "step_multi_kernel" : kernel_name(s->D, s->var));
+        *kernel = s->var < 0 ? ""
+                             : (cl ? "step_cluster_kernel"
+                                   : (s->multi_k > 1 ? "step_multi_kernel" : kernel_name(s->D, s->var)));
     return LBM_OK;
 }
 

@@ -65,6 +65,17 @@ cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStre
 constexpr int kMultiTX2 = 128;
 constexpr int kMultiChunk2 = 8;
 cudaError_t launch_step_multi_d2(int dtype, const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st);
+// K steps of a small periodic D2 lattice held in the shared memory of one
+// thread-block cluster (lbm_step_cluster.cuh), FP32 or FP64 storage, cluster
+// variant v (kClusterBase + v in reports).  cluster_fits_d2: the lattice fits
+// variant v (rows per block, shared memory).  probe = true only checks that
+// such a cluster can be resident on the device (no launch).
+constexpr int kClusterBase = 300;
+int n_cluster_variants();
+int cluster_blocks(int v);
+bool cluster_fits_d2(int dtype, int v, int nx, int ny);
+cudaError_t launch_step_cluster_d2(int dtype, int v, const StepArgs& a0, const StepArgs& a1, int K, cudaStream_t st,
+                                   bool probe = false);
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
                         void* b, long long N, cudaStream_t st);
 cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,

@@ -16,6 +16,7 @@ namespace lbm {
 // as deviations from the rest state: mass as rho - 1, energy as E - eref with
 // eref = D T0.  get() adds the references back in FP64.
 template <int K> struct DiagDev {
+    static constexpr bool kFF = true;  // reduced as float-float pairs (block_diagnostics)
     float d[K];
     int n;
     float eref;
@@ -36,6 +37,13 @@ template <int K> struct DiagDev {
     __device__ __forceinline__ double get(int k) const {
         return double(d[k]) + (k == 0 ? double(n) : (k == K - 1 ? double(n) * double(eref) : 0.0));
     }
+    // value k = (h + l) + cnt() * cref(k)
+    __device__ __forceinline__ void ff(int k, float& h, float& l) const {
+        h = d[k];
+        l = 0.0f;
+    }
+    __device__ __forceinline__ int cnt() const { return n; }
+    __device__ __forceinline__ float cref(int k) const { return k == 0 ? 1.0f : (k == K - 1 ? eref : 0.0f); }
 };
 
 // (u0, rho b) of one site as the float2 groups of the aux slots:

@@ -23,6 +23,7 @@ namespace lbm {
 template <typename R, int K> struct DiagAcc;
 
 template <int K> struct DiagAcc<double, K> {
+    static constexpr bool kFF = false;  // reduced in FP64 (block_diagnostics)
     double v[K];
     __device__ __forceinline__ DiagAcc() {
 #pragma unroll
@@ -33,6 +34,7 @@ template <int K> struct DiagAcc<double, K> {
 };
 
 template <int K> struct DiagAcc<float, K> {
+    static constexpr bool kFF = true;  // reduced as float-float pairs (block_diagnostics)
     float hi[K], lo[K];
     __device__ __forceinline__ DiagAcc() {
 #pragma unroll
@@ -46,7 +48,34 @@ template <int K> struct DiagAcc<float, K> {
         lo[k] = __fadd_rn(lo[k], err);
     }
     __device__ __forceinline__ double get(int k) const { return double(hi[k]) + double(lo[k]); }
+    // value k = (h + l) + cnt() * cref(k)
+    __device__ __forceinline__ void ff(int k, float& h, float& l) const {
+        h = hi[k];
+        l = lo[k];
+    }
+    __device__ __forceinline__ int cnt() const { return 0; }
+    __device__ __forceinline__ float cref(int) const { return 0.0f; }
 };
+
+// Float-float sum h + l += h2 + l2: TwoSum of the high parts (Knuth, TAOCP
+// vol. 2, 4.2.2), the low parts and the rounding error added.
+__device__ __forceinline__ void ff_add(float& h, float& l, float h2, float l2) {
+    const float s = __fadd_rn(h, h2);
+    const float bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
+    h = s;
+    l = __fadd_rn(__fadd_rn(l, l2), err);
+}
+
+// Warp sum of float-float pairs in a fixed tree order; lane 0 holds it.
+__device__ __forceinline__ void ff_warp_sum(float& h, float& l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, h, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, l, o);
+        ff_add(h, l, h2, l2);
+    }
+}
 
 // 1/x, correctly rounded (the same value as 1/x by IEEE division, in fewer
 // instructions than the division sequence).
@@ -369,63 +398,87 @@ __device__ __forceinline__ void site_collide(const StepArgs& a, I s, const R* c_
 // 32 * (D + 2) doubles of shared memory.
 template <int D, int NT, typename Acc>
 __device__ __forceinline__ void block_diagnostics(const StepArgs& a, const Acc& acc, double* red) {
+    constexpr int K = D + 2;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    if constexpr (Acc::kFF) {
+        // FP32 accumulators: float-float pairs and an exact site count through
+        // the warp tree (GB300's FP64 rate is a small fraction of its FP32
+        // rate); FP64 only for each warp's result
+        int n = acc.cnt();
 #pragma unroll
-    for (int k = 0; k < D + 2; ++k) {
-        double v = acc.get(k);
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp * (D + 2) + k] = v;
+        for (int k = 0; k < K; ++k) {
+            float h, l;
+            acc.ff(k, h, l);
+            ff_warp_sum(h, l);
+            if (lane == 0) red[warp * K + k] = (double(h) + double(l)) + double(n) * double(acc.cref(k));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double v = acc.get(k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * K + k] = v;
+        }
     }
     __syncthreads();
     const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     __shared__ int last;
-    if (tid == 0) {
-        for (int k = 0; k < D + 2; ++k) {
-            double v = 0.0;
-            for (int w = 0; w < NT / 32; ++w) v += red[w * (D + 2) + k];
-            a.partial[(long long)bid * (D + 2) + k] = v;
-        }
+    if (tid < K) {  // the warps in order, one value per thread
+        double v = 0.0;
+        for (int w = 0; w < NT / 32; ++w) v += red[w * K + tid];
+        a.partial[(long long)bid * K + tid] = v;
         __threadfence();
-        last = (atomicAdd(a.ticket, 1u) == nblocks - 1);
     }
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(a.ticket, 1u) == nblocks - 1);
     __syncthreads();
     if (!last) return;
     // The last block sums the per-block partials: thread t takes blocks
     // t, t + NT, ... in order, then the same fixed tree -- the result does not
     // depend on block scheduling.
     __threadfence();
-    double v[D + 2];
+    double v[K];
 #pragma unroll
-    for (int k = 0; k < D + 2; ++k) v[k] = 0.0;
+    for (int k = 0; k < K; ++k) v[k] = 0.0;
     for (unsigned int b2 = tid; b2 < nblocks; b2 += NT)
 #pragma unroll
-        for (int k = 0; k < D + 2; ++k) v[k] += __ldcg(a.partial + (long long)b2 * (D + 2) + k);
+        for (int k = 0; k < K; ++k) v[k] += __ldcg(a.partial + (long long)b2 * K + k);
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < D + 2; ++k) {
-        double x = v[k];
+    for (int k = 0; k < K; ++k) {
+        if constexpr (Acc::kFF) {
+            // the FP64 partial as a float-float pair (about 48 bits)
+            float h = __double2float_rn(v[k]);
+            float l = __double2float_rn(v[k] - double(h));
+            ff_warp_sum(h, l);
+            if (lane == 0) red[warp * K + k] = double(h) + double(l);
+        } else {
+            double x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp * (D + 2) + k] = x;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) red[warp * K + k] = x;
+        }
     }
     __syncthreads();
     double tot = 0.0;
-    if (tid < D + 2)
-        for (int w = 0; w < NT / 32; ++w) tot += red[w * (D + 2) + tid];
+    if (tid < K)
+        for (int w = 0; w < NT / 32; ++w) tot += red[w * K + tid];
     __syncthreads();
-    if (tid < D + 2) red[tid] = tot;
+    if (tid < K) red[tid] = tot;
     __syncthreads();
     if (tid == 0) {
         const long long st = *a.step_ctr;
         if (a.diag_out)
-            for (int k = 0; k < D + 2; ++k) a.diag_out[k] = red[k];
+            for (int k = 0; k < K; ++k) a.diag_out[k] = red[k];
         if (a.hist) {
             double* rec = a.hist + (st % a.hist_cap) * (D + 3);
             rec[0] = double(st);
-            for (int k = 0; k < D + 2; ++k) rec[1 + k] = red[k];
+            for (int k = 0; k < K; ++k) rec[1 + k] = red[k];
         }
         if (a.write_state) *a.step_ctr = st + 1;
         *a.ticket = 0u;

@@ -789,6 +789,7 @@ template <int D, typename FS, int TX, int TY, int MB, int PF, bool WS = false> s
 // packed FP32 as deviations from the rest state (mass as rho - 1, energy as
 // E - D T0), then in FP64 per block.
 template <int D> struct PairDiag {
+    static constexpr bool kFF = true;  // reduced as float-float pairs (block_diagnostics)
     using P = px::P;
     P m, e, j[D];
     float eref;
@@ -812,6 +813,16 @@ template <int D> struct PairDiag {
         if (k == D + 1) return double(e.a()) + double(e.b()) + double(n) * double(eref);
         return double(j[k - 1].a()) + double(j[k - 1].b());
     }
+    // value k = (h + l) + cnt() * cref(k): the two sites' sums as an exact
+    // float-float pair
+    __device__ __forceinline__ void ff(int k, float& h, float& l) const {
+        const P v = k == 0 ? m : (k == D + 1 ? e : j[k - 1]);
+        h = v.a();
+        l = 0.0f;
+        ff_add(h, l, v.b(), 0.0f);
+    }
+    __device__ __forceinline__ int cnt() const { return n; }
+    __device__ __forceinline__ float cref(int k) const { return k == 0 ? 1.0f : (k == D + 1 ? eref : 0.0f); }
 };
 
 template <int D, typename FS, int TX, int TY, int MB, int PF>

@@ -47,6 +47,7 @@ class lbm_opts(ctypes.Structure):
         ("model", ctypes.c_int),
         ("halo", ctypes.c_int),
         ("inplace", ctypes.c_int),
+        ("cluster", ctypes.c_int),
     ]
 
 
@@ -362,7 +363,7 @@ class Simulation:
     def __init__(self, dim, nx, ny=1, nz=1, tau=0.8, T0=1.0 / 3.0, bc="periodic", dtype="f64",
                  thermal=False, device=0, stream=None, tile=-1, chunk=0, diagnostics=True,
                  use_graphs=True, torch_allocator=False, steps_per_launch=0, model="bump", halo=0,
-                 inplace=False):
+                 inplace=False, cluster=0):
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -380,6 +381,7 @@ class Simulation:
         o.model = MODELS[model] if isinstance(model, str) else int(model)
         o.halo = int(halo)
         o.inplace = int(bool(inplace))
+        o.cluster = int(cluster)
         self.halo = int(halo)
         self._allocator = None
         if torch_allocator:

@@ -119,6 +119,15 @@ CONFIGS = {
     # would be negative)
     "std3d": dict(d=3, nx=256, ny=256, nz=256, tau=0.52, T0=1.0 / 3.0, thermal=False,
                   bc="periodic", steps=2000, dtype="f32", model="standard"),
+    # plane Poiseuille flow: half-way bounce-back walls normal to z, a
+    # uniform acceleration along x (u_max = a H^2 / (8 T tau) ~ 0.02 c at
+    # H = 256 once developed), from rest
+    "channel3d": dict(d=3, nx=256, ny=256, nz=256, tau=0.6, T0=0.1, thermal=False,
+                      bc="walls", steps=2000, dtype="f32", force=(1.0e-7, 0.0, 0.0)),
+    # the turb3d lattice and fields with the MRT collision of Appendix B:
+    # third- and fourth-order moments relaxed at their own rates
+    "mrt3d": dict(d=3, nx=256, ny=256, nz=256, tau=0.52, T0=0.05, thermal=False,
+                  bc="periodic", steps=2000, dtype="f32", mrt=(1.2, 1.4)),
 }
 
 
@@ -133,6 +142,12 @@ def fields_for(name, scale=None, seed=0):
     if name == "tgv2d":
         return taylor_green_pulse_2d(scale or c["nx"], c["T0"])
     if name == "turb3d":
+        n = scale or c["nx"]
+        return solenoidal_3d(n, k0=8.0 * n / 256.0, T0=c["T0"], thermal=c["thermal"], seed=seed)
+    if name == "channel3d":
+        n = scale or c["nx"]
+        return np.ones((n, n, n)), np.zeros((3, n, n, n)), np.full((n, n, n), c["T0"])
+    if name == "mrt3d":
         n = scale or c["nx"]
         return solenoidal_3d(n, k0=8.0 * n / 256.0, T0=c["T0"], thermal=c["thermal"], seed=seed)
     if name == "std3d":
