@@ -504,7 +504,7 @@ def run_serve(args):
         "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "requests": len(reqs),
                    "site_updates": updates, "step_unit": "one request (steps and ms_per_step count requests)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "kernel": "serve_kernel (cooperative, persistent over each round)"},
+                   "kernel": "serve_kernel (one cooperative launch per round of K steps, moments of finishing requests in the same launch; host loop pipelined one round deep)"},
         "serving": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                     "max_s": float(lat.max()), "wall_s": wall, "busy_s": busy, "rounds": rounds,
                     "offered_mlups": updates / max(reqs[-1]["t_arrival"], 1e-9) / 1e6,

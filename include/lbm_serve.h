@@ -27,8 +27,13 @@
  *    K is chosen so that a round lasts about opts.round_ms, so that newly
  *    admitted requests join within a round.  Requests of uneven sizes share
  *    every launch.
- *  - A finished simulation's moments are computed on the device and copied
- *    to host memory held by the server until lbm_server_poll returns them.
+ *  - A simulation that finishes within a round has its moments computed by
+ *    the same launch, after its last step; they are copied to host memory
+ *    held by the server until lbm_server_poll returns them.  The service
+ *    thread enqueues round i (admitted requests' field copies and start
+ *    kernels, the work list, the launch) before it waits for round i - 1 and
+ *    copies that round's results out, so the device does not wait for the
+ *    host between rounds.
  *  - Each result equals, bit for bit, that of the same request run alone
  *    through the server: tiles of different simulations never interact and
  *    the per-site arithmetic has no data-dependent ordering.

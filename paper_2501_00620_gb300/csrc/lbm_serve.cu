@@ -9,9 +9,15 @@
 // barrier between steps; it advances the round's K steps in one launch.  Each
 // simulation keeps its own A-B buffers, parity and step budget for the round.
 //
+// A simulation that finishes within a round has its moments computed in the
+// same launch, after the last step (the tile body with the state update off).
+//
 // Host side: a service thread admits queued requests first come first
-// served while their state fits the device pool, launches rounds, and
-// retires finished simulations (moments on the device, copy to host).
+// served while their state fits the device pool and launches rounds.  The
+// loop is pipelined one round deep: round i is enqueued (admissions' field
+// copies and start kernels, the work list, the launch) before the thread
+// waits for round i - 1 and copies its finished simulations' moments out, so
+// the device never waits for the host's bookkeeping.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -48,6 +54,8 @@ constexpr size_t kAlign = 256;
 
 struct ServeSim {
     StepArgs a[2];  // per-simulation arguments for input buffer 0 and 1
+    StepArgs am;    // moments of the state after the round (fin = 1): write_state 0, mout set
+    int fin;        // 1: the simulation finishes in this round
     void* f[2];
     void* b[2];
     int d, tiles_x, item0, steps, cur;
@@ -62,45 +70,58 @@ static_assert(kTX == kStripNT, "the strip body runs on the serve kernel's blocks
 constexpr size_t kmax(size_t x, size_t y) { return x > y ? x : y; }
 constexpr size_t kSmem = kmax(kmax(Sh1::smem, Sh1d::smem), (size_t)ShS::SMEM);
 
-// K steps of every simulation in `sims` (sorted by item0); work item `it`
-// belongs to the last simulation with item0 <= it.
+// One tile of simulation S with arguments a (a step, or the moments pass).
+__device__ __forceinline__ void serve_tile(const ServeSim& S, const StepArgs& a, int local, unsigned char* smem) {
+    if (S.d == 1) {
+        if (S.dt == DT_F64)
+            step_block<1, double, kTX, 1>(a, local, 0, 0, smem);
+        else
+            step_block<1, float, kTX, 1>(a, local, 0, 0, smem);
+    } else {
+        DiagDev<4> acc(0.0f);  // unused: no diagnostics in serving rounds
+        int bad = 0;
+        if (a.fixed_x)
+            strip_block<float, kTX, true, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+        else
+            strip_block<float, kTX, false, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
+        if (bad) atomicOr(a.flag, bad);
+    }
+    __syncthreads();  // the next work item reuses shared memory
+}
+
+// The simulation that work item `it` belongs to: the last with item0 <= it.
+__device__ __forceinline__ int serve_owner(const ServeSim* __restrict__ sims, int nsims, int it) {
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].item0 <= it)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// K steps of every simulation in `sims` (sorted by item0), then the moments
+// of the simulations that finish in this round.
 __global__ void __launch_bounds__(kTX, 2) serve_kernel(const ServeSim* __restrict__ sims, int nsims, int nitems,
                                                     int K) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::grid_group grid = cg::this_grid();
     for (int k = 0; k < K; ++k) {
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-            int lo = 0, hi = nsims - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sims[mid].item0 <= it)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            const ServeSim& S = sims[lo];
+            const ServeSim& S = sims[serve_owner(sims, nsims, it)];
             if (k >= S.steps) continue;  // uniform over the block
             // read in place (not copied to registers): the tile bodies load
             // the fields they need
-            const StepArgs& a = S.a[(S.cur + k) & 1];
-            const int local = it - S.item0;
-            if (S.d == 1) {
-                if (S.dt == DT_F64)
-                    step_block<1, double, kTX, 1>(a, local, 0, 0, smem);
-                else
-                    step_block<1, float, kTX, 1>(a, local, 0, 0, smem);
-            } else {
-                DiagDev<4> acc(0.0f);  // unused: no diagnostics in serving rounds
-                int bad = 0;
-                if (a.fixed_x)
-                    strip_block<float, kTX, true, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
-                else
-                    strip_block<float, kTX, false, true>(a, local % S.tiles_x, local / S.tiles_x, smem, acc, bad);
-                if (bad) atomicOr(a.flag, bad);
-            }
-            __syncthreads();  // the next work item reuses shared memory
+            serve_tile(S, S.a[(S.cur + k) & 1], it - S.item0, smem);
         }
         grid.sync();
+    }
+    // every step of the round is complete (the barrier above): moments
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const ServeSim& S = sims[serve_owner(sims, nsims, it)];
+        if (S.fin) serve_tile(S, S.am, it - S.item0, smem);
     }
 }
 
@@ -223,10 +244,13 @@ struct Server {
     cudaStream_t stream = nullptr;
     char* pool_mem = nullptr;
     Pool pool;
-    ServeSim* d_sims = nullptr;
-    ServeSim* h_sims = nullptr;  // pinned
-    int* h_flag = nullptr;       // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t cstream = nullptr;  // copies of finished simulations' moments
+    ServeSim* d_sims = nullptr;      // [2][max_active]: work lists of rounds i and i + 1
+    ServeSim* h_sims = nullptr;      // pinned, [2][max_active]
+    int* h_flag = nullptr;           // pinned
+    cudaEvent_t ev0[2] = {nullptr, nullptr}, ev1[2] = {nullptr, nullptr};
+    double* stage[2] = {nullptr, nullptr};  // pinned staging of admitted fields, per round parity
+    size_t stage_n[2] = {0, 0};             // doubles
     int grid_max = 0;
     std::chrono::steady_clock::time_point t0;
 
@@ -248,8 +272,8 @@ struct Server {
     double rate = 2e10;  // site updates per second, running estimate for the round length
 
     void loop();
-    bool admit_one(const std::shared_ptr<Request>& r);
-    void retire(const std::shared_ptr<Request>& r);
+    bool admit_one(const std::shared_ptr<Request>& r, double* staged);
+    bool finish(std::vector<std::shared_ptr<Request>>& done, int par, int nsims);
 };
 
 // 2D requests run on the strip kernel's tile body.
@@ -279,13 +303,14 @@ StepArgs sim_args(const Server& S, const Request& r) {
     return a;
 }
 
-// Device set-up of an admitted request (asynchronous on the server stream).
-bool Server::admit_one(const std::shared_ptr<Request>& r) {
+// Device set-up of an admitted request (asynchronous on the server stream):
+// its fields, already in pinned staging memory, are copied in and the start
+// state (and the reservoirs) computed.
+bool Server::admit_one(const std::shared_ptr<Request>& r, double* staged) {
     char* base = pool_mem + r->off;
     double* m = reinterpret_cast<double*>(base + r->lay.m);
     const long long N = r->N;
-    cudaError_t e = cudaMemcpyAsync(m, r->fields.data(), sizeof(double) * (2 + r->d) * N, cudaMemcpyHostToDevice,
-                                    stream);
+    cudaError_t e = cudaMemcpyAsync(m, staged, sizeof(double) * (2 + r->d) * N, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + r->lay.flag, 0, sizeof(int), stream);
     if (e == cudaSuccess)
         e = launch_init(r->d, r->dt, m, m + N, m + (1 + r->d) * N, base + r->lay.f[0], base + r->lay.b[0], N,
@@ -294,7 +319,9 @@ bool Server::admit_one(const std::shared_ptr<Request>& r) {
         e = launch_reservoir(r->d, r->dt, m, m + N, m + (1 + r->d) * N, r->nx, r->ny, N, base + r->lay.gf,
                              base + r->lay.gb, base + r->lay.gaux, stream);
     if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
         thread_error = std::string("admission: ") + cudaGetErrorString(e);
+        cv_done.notify_all();
         return false;
     }
     r->cur = 0;
@@ -302,37 +329,63 @@ bool Server::admit_one(const std::shared_ptr<Request>& r) {
     return true;
 }
 
-// Moments of a finished simulation into its host vector (blocking).
-void Server::retire(const std::shared_ptr<Request>& r) {
-    char* base = pool_mem + r->off;
-    StepArgs a = sim_args(*this, *r);
-    a.fin = base + r->lay.f[r->cur];
-    a.bin = base + r->lay.b[r->cur];
-    a.fout = base + r->lay.f[r->cur ^ 1];
-    a.bout = base + r->lay.b[r->cur ^ 1];
-    a.write_state = 0;
-    a.mout = reinterpret_cast<double*>(base + r->lay.m);
-    // the same tile body as the steps (strip kernel, variant 3, for 2D)
-    cudaError_t e = launch_step(r->d, r->dt, uses_strip(*r) ? 3 : 0, a, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r->fields.data(), a.mout, sizeof(double) * (2 + r->d) * r->N, cudaMemcpyDeviceToHost,
-                            stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, a.flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) thread_error = std::string("retire: ") + cudaGetErrorString(e);
-    r->flag = *h_flag;
+// Round `par` has completed on the device (the caller waited for its end
+// event): its time, and the results of the simulations that finished in it
+// (moments computed by the round itself) copied to their host vectors.
+bool Server::finish(std::vector<std::shared_ptr<Request>>& done, int par, int nsims) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0[par], ev1[par]);
+    double done_sites = 0;
+    const ServeSim* hs = h_sims + (size_t)par * opts.max_active;
+    for (int i = 0; i < nsims; ++i) done_sites += (double)hs[i].a[0].N * hs[i].steps;
+    if (ms > 0) rate = 0.5 * rate + 0.5 * done_sites / (ms * 1e-3);
+    cudaError_t e = cudaSuccess;
+    for (auto& r : done) {
+        char* base = pool_mem + r->off;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->fields.data(), base + r->lay.m, sizeof(double) * (2 + r->d) * r->N,
+                                cudaMemcpyDeviceToHost, cstream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_flag, base + r->lay.flag, sizeof(int), cudaMemcpyDeviceToHost, cstream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream);
+        r->flag = *h_flag;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    busy_s += ms * 1e-3;
+    ++rounds;
+    if (e != cudaSuccess) {
+        thread_error = std::string("results: ") + cudaGetErrorString(e);
+        cv_done.notify_all();
+        return false;
+    }
+    n_active -= (int)done.size();
+    for (auto& r : done) {
+        pool.release(r->off, r->lay.total);
+        r->t_done = now_s(t0);
+        r->state = 2;
+        ++n_completed;
+        site_updates += (double)r->N * r->steps;
+        last_done = r->t_done;
+    }
+    if (!done.empty()) cv_done.notify_all();
+    return true;
 }
 
 void Server::loop() {
     cudaSetDevice(device);
+    int par = 0;                 // parity of the round being enqueued
+    bool inflight = false;       // round 1 - par is on the device
+    int inflight_n = 0;          // its number of simulations
+    std::vector<std::shared_ptr<Request>> fin[2];  // simulations that finish in round par
     while (true) {
         std::vector<std::shared_ptr<Request>> admitted;
+        bool stopping = false;
         {
             std::unique_lock<std::mutex> lk(mu);
-            if (active.empty())
+            if (active.empty() && !inflight)
                 cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return stop || !queue.empty(); });
-            if (stop) return;
-            while (!queue.empty() && (int)(active.size() + admitted.size()) < opts.max_active) {
+            stopping = stop;
+            while (!stopping && !queue.empty() && (int)(active.size() + admitted.size()) < opts.max_active) {
                 auto r = queue.front();
                 const size_t off = pool.alloc(r->lay.total);
                 if (off == Pool::npos) break;
@@ -343,96 +396,126 @@ void Server::loop() {
                 ++n_active;
             }
         }
-        for (auto& r : admitted) {
-            if (!admit_one(r)) return;
-            active.push_back(r);
-        }
-        if (active.empty()) continue;
-
-        // one round: every active simulation advances min(K, remaining) steps
-        double sites = 0;
-        long max_rem = 0;
-        for (auto& r : active) {
-            sites += (double)r->N;
-            max_rem = std::max(max_rem, r->remaining);
-        }
-        long K = (long)(opts.round_ms * 1e-3 * rate / std::max(sites, 1.0));
-        K = std::max(1L, std::min({K, max_rem, 4096L}));
-        const int ns = (int)active.size();
-        int items = 0;
-        for (int i = 0; i < ns; ++i) {
-            const Request& r = *active[i];
-            char* base = pool_mem + r.off;
-            ServeSim& s = h_sims[i];
-            for (int k = 0; k < 2; ++k) {
-                s.f[k] = base + r.lay.f[k];
-                s.b[k] = base + r.lay.b[k];
-            }
-            for (int k = 0; k < 2; ++k) {
-                s.a[k] = sim_args(*this, r);
-                s.a[k].fin = s.f[k];
-                s.a[k].bin = s.b[k];
-                s.a[k].fout = s.f[k ^ 1];
-                s.a[k].bout = s.b[k ^ 1];
-            }
-            s.d = r.d;
-            s.dt = r.dt;
-            s.strip = uses_strip(r) ? 1 : 0;
-            s.tiles_x = s.strip ? (r.nx + ShS::TX - 1) / ShS::TX : (r.nx + kTX - 1) / kTX;
-            s.item0 = items;
-            s.steps = (int)std::min(K, r.remaining);
-            s.cur = r.cur;
-            items += s.tiles_x * (r.d == 2 ? (r.ny + kChunk2 - 1) / kChunk2 : 1);
-        }
-        cudaError_t e = cudaMemcpyAsync(d_sims, h_sims, sizeof(ServeSim) * ns, cudaMemcpyHostToDevice, stream);
-        int grid = std::max(1, std::min(grid_max, items));
-        int Ki = (int)K;
-        void* args[] = {&d_sims, (void*)&ns, &items, &Ki};
-        if (e == cudaSuccess) e = cudaEventRecord(ev0, stream);
-        if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void*)serve_kernel, dim3(grid), dim3(kTX), args, kSmem, stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev1, stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
-        if (e != cudaSuccess) {
-            std::lock_guard<std::mutex> lk(mu);
-            thread_error = std::string("round: ") + cudaGetErrorString(e);
-            cv_done.notify_all();
+        if (stopping) {
+            cudaStreamSynchronize(stream);  // nothing of the server in flight on return
             return;
         }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, ev0, ev1);
-        double done_sites = 0;
-        for (int i = 0; i < ns; ++i) done_sites += (double)active[i]->N * h_sims[i].steps;
-        if (ms > 0) rate = 0.5 * rate + 0.5 * done_sites / (ms * 1e-3);
-
-        std::vector<std::shared_ptr<Request>> still;
-        std::vector<std::shared_ptr<Request>> finished;
-        for (int i = 0; i < ns; ++i) {
-            auto& r = active[i];
-            r->remaining -= h_sims[i].steps;
-            r->cur ^= (h_sims[i].steps & 1);
-            if (r->remaining <= 0)
-                finished.push_back(r);
-            else
-                still.push_back(r);
-        }
-        active.swap(still);
-        for (auto& r : finished) retire(r);
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            busy_s += ms * 1e-3;
-            ++rounds;
-            n_active -= (int)finished.size();
-            for (auto& r : finished) {
-                pool.release(r->off, r->lay.total);
-                r->t_done = now_s(t0);
-                r->state = 2;
-                ++n_completed;
-                site_updates += (double)r->N * r->steps;
-                last_done = r->t_done;
+        // admissions: fields into this parity's pinned staging (its last
+        // copies, two rounds ago, have completed), then onto the device
+        if (!admitted.empty()) {
+            size_t need = 0;
+            for (auto& r : admitted) need += (size_t)(2 + r->d) * r->N;
+            if (need > stage_n[par]) {
+                if (stage[par]) cudaFreeHost(stage[par]);
+                stage[par] = nullptr;
+                stage_n[par] = 0;
+                if (cudaMallocHost(&stage[par], sizeof(double) * need) != cudaSuccess) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    thread_error = "admission: pinned staging memory";
+                    cv_done.notify_all();
+                    return;
+                }
+                stage_n[par] = need;
             }
-            if (!finished.empty()) cv_done.notify_all();
+            size_t o = 0;
+            for (auto& r : admitted) {
+                const size_t n = (size_t)(2 + r->d) * r->N;
+                std::memcpy(stage[par] + o, r->fields.data(), sizeof(double) * n);
+                if (!admit_one(r, stage[par] + o)) return;
+                active.push_back(r);
+                o += n;
+            }
         }
+
+        // round i: every active simulation advances min(K, remaining) steps;
+        // the host's copy of each simulation's step count and parity moves
+        // ahead at once (the device follows in stream order)
+        int ns = (int)active.size();
+        fin[par].clear();
+        if (ns > 0) {
+            double sites = 0;
+            long max_rem = 0;
+            for (auto& r : active) {
+                sites += (double)r->N;
+                max_rem = std::max(max_rem, r->remaining);
+            }
+            long K = (long)(opts.round_ms * 1e-3 * rate / std::max(sites, 1.0));
+            K = std::max(1L, std::min({K, max_rem, 4096L}));
+            ServeSim* hs = h_sims + (size_t)par * opts.max_active;
+            ServeSim* ds = d_sims + (size_t)par * opts.max_active;
+            int items = 0;
+            std::vector<std::shared_ptr<Request>> still;
+            for (int i = 0; i < ns; ++i) {
+                const auto& rp = active[i];
+                const Request& r = *rp;
+                char* base = pool_mem + r.off;
+                ServeSim& sm = hs[i];
+                for (int k = 0; k < 2; ++k) {
+                    sm.f[k] = base + r.lay.f[k];
+                    sm.b[k] = base + r.lay.b[k];
+                }
+                for (int k = 0; k < 2; ++k) {
+                    sm.a[k] = sim_args(*this, r);
+                    sm.a[k].fin = sm.f[k];
+                    sm.a[k].bin = sm.b[k];
+                    sm.a[k].fout = sm.f[k ^ 1];
+                    sm.a[k].bout = sm.b[k ^ 1];
+                }
+                sm.d = r.d;
+                sm.dt = r.dt;
+                sm.strip = uses_strip(r) ? 1 : 0;
+                sm.tiles_x = sm.strip ? (r.nx + ShS::TX - 1) / ShS::TX : (r.nx + kTX - 1) / kTX;
+                sm.item0 = items;
+                sm.steps = (int)std::min(K, r.remaining);
+                sm.cur = r.cur;
+                const int after = r.cur ^ (sm.steps & 1);
+                sm.fin = r.remaining - sm.steps <= 0;
+                if (sm.fin) {
+                    // moments of the final state, as lbm_moments computes them
+                    sm.am = sm.a[after];
+                    sm.am.write_state = 0;
+                    sm.am.mout = reinterpret_cast<double*>(base + r.lay.m);
+                }
+                items += sm.tiles_x * (r.d == 2 ? (r.ny + kChunk2 - 1) / kChunk2 : 1);
+                rp->remaining -= sm.steps;
+                rp->cur = after;
+                if (sm.fin)
+                    fin[par].push_back(rp);
+                else
+                    still.push_back(rp);
+            }
+            cudaError_t e = cudaMemcpyAsync(ds, hs, sizeof(ServeSim) * ns, cudaMemcpyHostToDevice, stream);
+            int grid = std::max(1, std::min(grid_max, items));
+            int Ki = (int)K;
+            void* args[] = {&ds, (void*)&ns, &items, &Ki};
+            if (e == cudaSuccess) e = cudaEventRecord(ev0[par], stream);
+            if (e == cudaSuccess)
+                e = cudaLaunchCooperativeKernel((const void*)serve_kernel, dim3(grid), dim3(kTX), args, kSmem, stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev1[par], stream);
+            if (e != cudaSuccess) {
+                std::lock_guard<std::mutex> lk(mu);
+                thread_error = std::string("round: ") + cudaGetErrorString(e);
+                cv_done.notify_all();
+                return;
+            }
+            active.swap(still);
+        }
+
+        // round i - 1: wait for it (round i is queued behind it), then its
+        // results
+        if (inflight) {
+            if (cudaEventSynchronize(ev1[par ^ 1]) != cudaSuccess) {
+                std::lock_guard<std::mutex> lk(mu);
+                thread_error = "round: the batched launch failed";
+                cv_done.notify_all();
+                return;
+            }
+            if (!finish(fin[par ^ 1], par ^ 1, inflight_n)) return;
+            fin[par ^ 1].clear();
+        }
+        inflight = ns > 0;
+        inflight_n = ns;
+        if (ns > 0) par ^= 1;
     }
 }
 
@@ -496,9 +579,12 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (S.pool_mem) cudaFree(S.pool_mem);
         if (S.h_sims) cudaFreeHost(S.h_sims);
         if (S.h_flag) cudaFreeHost(S.h_flag);
-        if (S.ev0) cudaEventDestroy(S.ev0);
-        if (S.ev1) cudaEventDestroy(S.ev1);
+        for (int k = 0; k < 2; ++k) {
+            if (S.ev0[k]) cudaEventDestroy(S.ev0[k]);
+            if (S.ev1[k]) cudaEventDestroy(S.ev1[k]);
+        }
         if (S.stream) cudaStreamDestroy(S.stream);
+        if (S.cstream) cudaStreamDestroy(S.cstream);
         delete h;
         return lbm::serve::fail(LBM_ECUDA, m);
     };
@@ -510,11 +596,13 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     if (o.hbm_budget == 0) o.hbm_budget = free_b / 2;
     S.opts.hbm_budget = o.hbm_budget;
     if ((e = cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&S.cstream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&S.pool_mem, o.hbm_budget)) != cudaSuccess ||
-        (e = cudaMalloc(&S.d_sims, sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
-        (e = cudaMallocHost(&S.h_sims, sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
+        (e = cudaMalloc(&S.d_sims, 2 * sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
+        (e = cudaMallocHost(&S.h_sims, 2 * sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
         (e = cudaMallocHost(&S.h_flag, sizeof(int))) != cudaSuccess ||
-        (e = cudaEventCreate(&S.ev0)) != cudaSuccess || (e = cudaEventCreate(&S.ev1)) != cudaSuccess)
+        (e = cudaEventCreate(&S.ev0[0])) != cudaSuccess || (e = cudaEventCreate(&S.ev1[0])) != cudaSuccess ||
+        (e = cudaEventCreate(&S.ev0[1])) != cudaSuccess || (e = cudaEventCreate(&S.ev1[1])) != cudaSuccess)
         return cleanup(std::string("server set-up: ") + cudaGetErrorString(e));
     S.pool.reset(S.pool_mem, o.hbm_budget);
     int per_sm = 0, sms = 0;
@@ -624,13 +712,18 @@ void lbm_server_destroy(lbm_server* h) {
     S.cv_work.notify_all();
     if (S.worker.joinable()) S.worker.join();
     cudaStreamSynchronize(S.stream);
+    cudaStreamSynchronize(S.cstream);
     cudaFree(S.d_sims);
     cudaFree(S.pool_mem);
     cudaFreeHost(S.h_sims);
     cudaFreeHost(S.h_flag);
-    cudaEventDestroy(S.ev0);
-    cudaEventDestroy(S.ev1);
+    for (int k = 0; k < 2; ++k) {
+        cudaEventDestroy(S.ev0[k]);
+        cudaEventDestroy(S.ev1[k]);
+        if (S.stage[k]) cudaFreeHost(S.stage[k]);
+    }
     cudaStreamDestroy(S.stream);
+    cudaStreamDestroy(S.cstream);
     delete h;
 }
 
