@@ -877,16 +877,23 @@ lbm_status lbm_init(lbm_sim* s, const lbm_fields_in* in) {
     if (!s || !in || !in->rho || !in->u || !in->T) return fail(LBM_EINVAL, "NULL argument");
     DeviceGuard dg(s->device);
     const long long N = s->N;
-    for (long long k = 0; k < N; ++k)
-        if (!(in->rho[k] > 0) || !(in->T[k] > 0)) return fail(LBM_EINVAL, "rho and T must be positive");
     lbm_status st = ensure_fields(s);
     if (st != LBM_OK) return st;
     double* rho = s->fields;
     double* u = rho + N;
     double* T = u + (size_t)s->D * N;
     CK(cudaMemcpyAsync(rho, in->rho, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(u, in->u, (size_t)s->D * N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(T, in->T, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    // positivity of rho and T checked on the device while u is copied; the
+    // state is touched only once the check has passed
+    int* bad = s->flag + 1;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s->stream));
+    CK(launch_check_fields(rho, T, N, bad, s->stream));
+    CK(cudaMemcpyAsync(u, in->u, (size_t)s->D * N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (hbad) return fail(LBM_EINVAL, "rho and T must be positive");
     s->cur = 0;
     if (s->opts.model == LBM_MODEL_STANDARD) {
         CK(launch_std_init(s->D, s->dtype, rho, u, T, s->f[0], N, s->stream));
@@ -1136,15 +1143,20 @@ lbm_status lbm_diagnostics_history(lbm_sim* s, double* out, int cap, int* count)
 lbm_status lbm_last_diagnostics(lbm_sim* s, double* out) {
     if (!s || !out) return fail(LBM_EINVAL, "NULL argument");
     DeviceGuard dg(s->device);
+    // the step counter and the status flag in one wait, then the record
     long long ctr = 0;
+    int h = 0;
     CK(cudaMemcpyAsync(&ctr, s->step_ctr, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&h, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     if (ctr <= 0) return fail(LBM_EINVAL, "no diagnostics recorded yet");
     const int rec = s->D + 3;
     CK(cudaMemcpyAsync(out, s->hist + ((ctr - 1) % kHistCap) * rec, rec * sizeof(double), cudaMemcpyDeviceToHost,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    return check_flag(s);
+    if (h & 4) return fail(LBM_ETIMEOUT, "a bounded device-side wait for a tile copy gave up");
+    if (h & 1) return fail(LBM_EUNSTABLE, "state became non-physical (rho <= 0 or not finite)");
+    return LBM_OK;
 }
 
 lbm_status lbm_get_state(lbm_sim* s, double* f, double* b) {

@@ -1,4 +1,6 @@
 // Dimension dispatch for the kernel launchers.
+#include <algorithm>
+
 #include "lbm_internal.h"
 #include "lbm_fast_launch.cuh"
 #include "lbm_pair_launch.cuh"
@@ -109,6 +111,24 @@ dim3 step_grid(int D, int v, int nx, int ny, int nz, int chunk) {
 cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t st) {
     return LBM_BY_D(D, launch_step_d1(dtype, v, a, st), launch_step_d2(dtype, v, a, st),
                     launch_step_d3(dtype, v, a, st), cudaErrorInvalidValue);
+}
+
+// Grid-stride scan of the start fields on the device (a host loop over
+// N values would cost more than the copy of them).  Writes only on failure.
+__global__ void check_fields_kernel(const double* __restrict__ rho, const double* __restrict__ T, long long N,
+                                    int* bad) {
+    bool ok = true;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+         k += (long long)gridDim.x * blockDim.x)
+        ok &= (rho[k] > 0.0) && (T[k] > 0.0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) *bad = 1;
+}
+
+cudaError_t launch_check_fields(const double* rho, const double* T, long long N, int* bad, cudaStream_t st) {
+    const long long want = (N + 255) / 256;
+    const int blocks = (int)std::max(1LL, std::min<long long>(want, 8LL * device_sms()));
+    check_fields_kernel<<<blocks, 256, 0, st>>>(rho, T, N, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f, void* b,

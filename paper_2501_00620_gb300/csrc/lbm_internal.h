@@ -78,6 +78,9 @@ cudaError_t launch_step_cluster_d2(int dtype, int v, const StepArgs& a0, const S
                                    bool probe = false);
 cudaError_t launch_init(int D, int dtype, const double* rho, const double* u, const double* T, void* f,
                         void* b, long long N, cudaStream_t st);
+// Sets *bad (device) to 1 if some rho[k] or T[k] (k < N, device arrays) is
+// not > 0 (NaN included); leaves it unchanged otherwise.
+cudaError_t launch_check_fields(const double* rho, const double* T, long long N, int* bad, cudaStream_t st);
 cudaError_t launch_reservoir(int D, int dtype, const double* rho, const double* u, const double* T, int nx,
                              long long rows, long long N, void* gf, void* gb, void* gaux, cudaStream_t st);
 cudaError_t launch_get_state(int D, int dtype, const void* f, const void* b, double* fo, double* bo,

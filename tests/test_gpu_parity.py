@@ -682,3 +682,26 @@ def test_steps_per_launch_equal_single_steps(dtype):
     for (f, b), h in out[1:]:
         assert np.array_equal(f, f1) and np.array_equal(b, b1)
         assert len(h) == 42 and np.array_equal(h, h1)
+
+
+def test_init_refuses_non_positive_fields_and_keeps_state():
+    """lbm_init checks rho > 0 and T > 0 on the device; a refused call leaves
+    the state of the previous lbm_init untouched."""
+    d, nx = 2, 64
+    rho, u, T = W.taylor_green_pulse_2d(n=64, T0=0.2)
+    ny = nx
+    g = lbm.Simulation(d, nx, ny, 1, tau=0.6, T0=0.2, bc="periodic", dtype="f64")
+    g.init(rho, u, T)
+    g.step(3)
+    before = g.emitted()
+    for field, k, bad in (("rho", 17, -1.0), ("T", nx * ny - 1, 0.0), ("rho", 5, np.nan)):
+        r2, T2 = rho.copy(), T.copy()
+        (r2 if field == "rho" else T2).reshape(-1)[k] = bad
+        with pytest.raises(lbm.LBMError):
+            g.init(r2, u, T2)
+        after = g.emitted()
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+    g.init(rho, u, T)  # a valid call still works
+    g.step(1)
+    g.close()
