@@ -76,6 +76,9 @@ def parse(argv=None):
                    help="steps without the per-step conservation sums (lbm_opts.diagnostics = 0)")
     p.add_argument("--inplace", action="store_true",
                    help="the in-place step (one population buffer, two passes per step)")
+    p.add_argument("--no-others", action="store_true",
+                   help="skip the short measurements of the other workloads that follow the default "
+                        "(turb3d, one GPU) line's own measurement")
     p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
     p.add_argument("--no-sequential", action="store_true", help="serve: skip the one-at-a-time comparison")
     return p.parse_args(argv)
@@ -196,8 +199,10 @@ def hbm_peak():
         return 6800.0, "of fallback"
 
 
-KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_step.cuh", "lbm_mrt.cuh", "lbm_tma.cuh",
-                  "lbm_lean.cuh", "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
+# the staged kernel's device code (it compiles from these headers alone) and its
+# tile table
+KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_tma.cuh", "lbm_lean.cuh",
+                  "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
 
 
 def _code_only(text):
@@ -532,6 +537,71 @@ def run_serve(args):
         dist.destroy_process_group()
 
 
+# Short measurements of the other workloads, run after the headline one (outside
+# its timed region) so that one default bench run reports every kernel family:
+# (workload, storage, timed steps, warm-up steps).  Each is timed with CUDA
+# events on its own stream after the autotuner has run, like the headline.
+OTHER_WORKLOADS = (("tgv2d", "f32", 50, 5), ("tgv2d", "f16", 50, 5), ("tgv2d", "bf16", 50, 5),
+                   ("std3d", "f32", 40, 5), ("channel3d", "f32", 5, 3), ("mrt3d", "f32", 5, 3),
+                   ("sound1d", "f64", 2000, 5), ("riemann1d", "f64", 5000, 5), ("riemann1d", "f32", 1000, 5))
+
+
+def measure_others(local, fields_cache):
+    import numpy as np
+    import torch
+    from paper_2501_00620_gb300 import lbm
+    from paper_2501_00620_gb300 import workloads as W
+    peak, peak_src = hbm_peak()
+    out = []
+    for name, dtype, steps, warm in OTHER_WORKLOADS:
+        c = workload_params(name, dtype)
+        d, nx, ny, nz = c["d"], c["nx"], c["ny"], c["nz"]
+        N = nx * ny * nz
+        if name in ("mrt3d", "std3d") and "turb3d" in fields_cache:
+            # the turb3d fields (std3d: at its own uniform T0)
+            rho, u, T = fields_cache["turb3d"]
+            if name == "std3d":
+                T = np.full_like(rho, c["T0"])
+        else:
+            if name not in fields_cache:
+                fields_cache[name] = W.fields_for(name)
+            rho, u, T = fields_cache[name]
+        stream = torch.cuda.Stream(device=local)
+        sim = lbm.Simulation(d, nx, ny, nz, tau=c["tau"], T0=c["T0"], bc=c["bc"], dtype=dtype,
+                             thermal=c["thermal"], device=local, stream=stream.cuda_stream,
+                             model=c.get("model", "bump"))
+        sim.init(rho, u, T)
+        apply_settings(sim, c)
+        sim.step(warm)
+        sim.sync()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        status = "ok"
+        try:
+            sim.moments()
+        except lbm.LBMError as e:
+            status = "unstable" if e.status == lbm.LBM_EUNSTABLE else "error %d" % e.status
+        tile, chunk, kernel = sim.launch_config()
+        sim.close()
+        bps = algorithmic_bytes_per_site(d, dtype, c.get("model", "bump"))
+        rec = {"workload": name, "storage": dtype, "sites": N, "steps": steps,
+               "ms_per_step": ms / steps, "mlups": N * steps / (ms * 1e-3) / 1e6,
+               "kernel": kernel, "tile": tile, "chunk": chunk, "final_state": status}
+        if d > 1:
+            ach = N * bps / (ms / steps * 1e-3) / 1e9
+            rec["roofline"] = {"bytes_per_site": bps, "achieved_gbs": ach, "frac": ach / peak,
+                               "peak_source": peak_src}
+        else:
+            rec["time_to_result_ms"] = ms
+        out.append(rec)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -652,6 +722,11 @@ def main():
                "sample": "%s on %d sites (%s), %d steps, %.1f s" % (
                    name, sites, "x".join([str(n)] * d) if d > 1 else str(n), steps_cpu, dt)}
 
+    others = None
+    if name == "turb3d" and world == 1 and not args.no_others and not args.scale and args.tile < 0:
+        sim.close()
+        others = measure_others(local, {"turb3d": (rho, u, T)})
+
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -676,6 +751,13 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if others is not None:
+        line["other_workloads"] = {
+            "how": "after the headline measurement, same process and GPU: each workload created, "
+                   "initialised, warmed up (autotuner), then its timed steps between CUDA events on its "
+                   "own stream; diagnostics recorded every step; roofline frac of measured HBM on the "
+                   "algorithmic bytes per site; 1D lattices report time to result",
+            "results": others}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -405,13 +405,11 @@ __global__ void __launch_bounds__(TX* TY) step_multi_kernel(const StepArgs a0, c
 // Start: every site emits its local equilibrium, df = f^eq(rho, u) - w,
 // bt = b^eq(u, T) + I/3 = T I + u u / 3 (Eq. 36, Appendix A).
 template <int D, typename FS>
-__global__ void init_kernel(const double* __restrict__ rho, const double* __restrict__ u,
-                            const double* __restrict__ T, FS* __restrict__ f,
-                            typename Store<FS>::breal* __restrict__ b, long long N) {
+__device__ __forceinline__ void init_site(const double* __restrict__ rho, const double* __restrict__ u,
+                                          const double* __restrict__ T, FS* __restrict__ f,
+                                          typename Store<FS>::breal* __restrict__ b, long long N, long long s) {
     using L = Lattice<D>;
     using real = typename Store<FS>::real;
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= N) return;
     real uu[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) uu[c] = real(u[c * N + s]);
@@ -426,16 +424,23 @@ __global__ void init_kernel(const double* __restrict__ rho, const double* __rest
             b[BLayout<D, FS>::at(sym<D>(c, d2), s, N)] = uu[c] * uu[d2] * real(1.0 / 3.0) + (c == d2 ? real(T[s]) : real(0));
 }
 
+template <int D, typename FS>
+__global__ void init_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                            const double* __restrict__ T, FS* __restrict__ f,
+                            typename Store<FS>::breal* __restrict__ b, long long N) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s < N) init_site<D, FS>(rho, u, T, f, b, N, s);
+}
+
 // Reservoirs of the fixed-state boundary: for each row, the equilibrium of the
 // edge site's initial state (side 0: x = 0, side 1: x = nx - 1).
 template <int D, typename R>
-__global__ void reservoir_kernel(const double* __restrict__ rho, const double* __restrict__ u,
-                                 const double* __restrict__ T, int nx, long long rows, long long N,
-                                 R* __restrict__ gf, R* __restrict__ gb, R* __restrict__ gaux) {
+__device__ __forceinline__ void reservoir_item(const double* __restrict__ rho, const double* __restrict__ u,
+                                               const double* __restrict__ T, int nx, long long rows, long long N,
+                                               R* __restrict__ gf, R* __restrict__ gb, R* __restrict__ gaux,
+                                               long long t) {
     using L = Lattice<D>;
     constexpr int NB = L::NB, NAUX = D + NB;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= 2 * rows) return;
     const int side = (int)(t / rows);
     const long long row = t % rows;
     const long long s = (side ? nx - 1 : 0) + (long long)nx * row;
@@ -459,6 +464,14 @@ __global__ void reservoir_kernel(const double* __restrict__ rho, const double* _
             // rho*b of a site at equilibrium: rho (b^eq) = rho (bt - I/3)
             gaux[((long long)side * NAUX + D + k) * rows + row] = r * (bt - (c == d2 ? R(1.0 / 3.0) : R(0)));
         }
+}
+
+template <int D, typename R>
+__global__ void reservoir_kernel(const double* __restrict__ rho, const double* __restrict__ u,
+                                 const double* __restrict__ T, int nx, long long rows, long long N,
+                                 R* __restrict__ gf, R* __restrict__ gb, R* __restrict__ gaux) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < 2 * rows) reservoir_item<D, R>(rho, u, T, nx, rows, N, gf, gb, gaux, t);
 }
 
 // Emitted state <-> FP64 planes of fbar*_i and bbar* (unshifted).
