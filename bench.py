@@ -470,6 +470,7 @@ def run_serve(args):
     wall = max_over_ranks(st["last_done_s"] - max(st["first_submit_s"], base["last_done_s"]), dist)
     busy = st["busy_s"] - base["busy_s"]
     rounds = st["rounds"] - base["rounds"]
+    launches = st["kernel_launches"] - base["kernel_launches"]
     value = whole_job_rate(updates, world, wall) / 1e6
 
     seq = None
@@ -509,9 +510,12 @@ def run_serve(args):
         "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "requests": len(reqs),
                    "site_updates": updates, "step_unit": "one request (steps and ms_per_step count requests)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "kernel": "serve_kernel (one cooperative launch per round of K steps, moments of finishing requests in the same launch; host loop pipelined one round deep)"},
+                   "kernel": "serve_kernel (persistent cooperative kernel: rounds of K steps posted through a "
+                             "mapped-memory mailbox, start states and moments of admitted and finishing requests "
+                             "computed in their rounds; host loop pipelined one round deep)"},
         "serving": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                     "max_s": float(lat.max()), "wall_s": wall, "busy_s": busy, "rounds": rounds,
+                    "kernel_launches": launches,
                     "offered_mlups": updates / max(reqs[-1]["t_arrival"], 1e-9) / 1e6,
                     "unstable_requests": len(unstable),
                     "unstable_also_in_fp64_oracle": (sum(1 for q in unstable if q["id"] in oracle_fatal)
@@ -521,14 +525,14 @@ def run_serve(args):
                     "sequential": seq},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": peak_src,
-                     "kernel": "serve_kernel", "launches": rounds,
-                     "duration": "CUDA events around each batched launch (busy_s)"},
+                     "kernel": "serve_kernel", "launches": launches, "rounds": rounds,
+                     "duration": "device clock (%globaltimer) at the start and end of each round (busy_s)"},
         "cpu_baseline": None,
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / len(reqs),
                 "d2h_bytes_per_step": h2d / len(reqs),
                 "includes": "per request: fields copied in at submit, results copied out at completion; "
                             "time from first submit to last completion"},
-        "gpu_launches": rounds,
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -695,17 +699,21 @@ def main():
         barrier()
         t0 = time.perf_counter()
         lbm.lbm_init(sim.h, hr, hu, hT)
+        t1 = time.perf_counter()
         for _ in range(args.steps):
             lbm.lbm_step(sim.h, 1)
             lbm.lbm_last_diagnostics(sim.h, rec)
+        t2 = time.perf_counter()
         lbm.lbm_moments(sim.h, orr, ou, oT)
-        te = max_over_ranks(time.perf_counter() - t0, dist)
+        t3 = time.perf_counter()
+        te = max_over_ranks(t3 - t0, dist)
         h2d = (2 + d) * N * 8
         d2h = (d + 3) * 8 * args.steps + (2 + d) * N * 8
         e2e = {"value": whole_job_rate(N * args.steps, world, te) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "lbm_init from pinned host fields, per step lbm_step(1) + lbm_last_diagnostics "
-                           "(d+3 doubles D2H), final lbm_moments (rho, u, T D2H)"}
+                           "(d+3 doubles D2H), final lbm_moments (rho, u, T D2H)",
+               "phases_ms": {"init": 1e3 * (t1 - t0), "steps": 1e3 * (t2 - t1), "moments": 1e3 * (t3 - t2)}}
 
     if rank != 0:
         if dist is not None:

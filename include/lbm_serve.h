@@ -21,19 +21,26 @@
  *    served, while their state fits in the server's device memory pool (the
  *    HBM budget) and the number of active simulations is below the limit.
  *    Admitted simulations stay resident on the device until they finish.
- *  - Every round, one cooperative (persistent) kernel advances all active
- *    simulations by up to K steps: its thread blocks walk a work list of
- *    tiles of every simulation, with a grid-wide barrier between steps.
- *    K is chosen so that a round lasts about opts.round_ms, so that newly
- *    admitted requests join within a round.  Requests of uneven sizes share
- *    every launch.
- *  - A simulation that finishes within a round has its moments computed by
- *    the same launch, after its last step; they are copied to host memory
+ *  - One persistent cooperative kernel advances all active simulations,
+ *    round after round, by up to K steps a round: its thread blocks walk a
+ *    work list of tiles of every simulation, with a grid-wide barrier between
+ *    steps.  The service thread posts each round through a mailbox in mapped
+ *    host memory (after the round's work list and the admitted requests'
+ *    fields have been copied to the device); the kernel computes the
+ *    admitted simulations' start states itself at the start of their first
+ *    round, runs the round, and reports it done in the mailbox.  K is chosen
+ *    so that a round lasts about opts.round_ms, so that newly admitted
+ *    requests join within a round.  Requests of uneven sizes share every
+ *    round.  Every wait of the kernel is bounded: after opts.idle_ms without
+ *    a posted round (or when the server stops) it leaves, and the service
+ *    thread launches it again when work arrives.
+ *  - A simulation that finishes within a round has its moments computed in
+ *    the same round, after its last step; they are copied to host memory
  *    held by the server until lbm_server_poll returns them.  The service
- *    thread enqueues round i (admitted requests' field copies and start
- *    kernels, the work list, the launch) before it waits for round i - 1 and
- *    copies that round's results out, so the device does not wait for the
- *    host between rounds.
+ *    thread posts round i before it waits for round i - 1 and copies that
+ *    round's results out (copies only, on a second stream, while the kernel
+ *    runs round i), so the device does not wait for the host between
+ *    rounds.
  *  - Each result equals, bit for bit, that of the same request run alone
  *    through the server: tiles of different simulations never interact and
  *    the per-site arithmetic has no data-dependent ordering.
@@ -60,7 +67,10 @@ typedef struct {
                            0: half of the device's free memory at creation */
     int max_active;     /* simulations advanced together; 0: 4096 */
     int device;         /* CUDA device ordinal, default 0 */
-    double round_ms;    /* target duration of one batched launch; 0: 2 ms */
+    double round_ms;    /* target duration of one round of K steps; 0: 2 ms */
+    double idle_ms;     /* the persistent kernel leaves after this long without
+                           a round to run (it is launched again when work
+                           arrives); 0: 50 ms */
 } lbm_server_opts;
 
 typedef struct {
@@ -79,10 +89,11 @@ typedef struct {
     uint64_t submitted, completed;  /* requests so far */
     int active, queued;             /* now */
     double site_updates;            /* sum over completed requests of sites x steps */
-    double busy_s;                  /* device time of the batched launches */
-    uint64_t rounds;                /* batched launches so far */
+    double busy_s;                  /* device time of the rounds (kernel clock) */
+    uint64_t rounds;                /* rounds completed so far */
     double first_submit_s, last_done_s;  /* host clock (seconds since server creation) */
     size_t pool_bytes, pool_in_use;
+    uint64_t kernel_launches;       /* launches of the persistent kernel so far */
 } lbm_server_stats;
 
 typedef struct lbm_server lbm_server;

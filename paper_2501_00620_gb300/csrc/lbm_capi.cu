@@ -46,7 +46,7 @@ size_t rbytes_of(int dtype) { return dtype == DT_F64 ? 8 : 4; }
 
 // autotune cache: (D, dtype, nx, ny, nz) -> (variant, chunk)
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune;
 
 const int kHistCap = 4096;
 
@@ -199,7 +199,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // staged, strip and serving kernels serve periodic and fixed-state lattices.
 bool small_t_on(const lbm_sim* s) { return s->small_t > 0 && s->opts.thermal && s->dtype != DT_F64; }
 bool generic_only(const lbm_sim* s) { return s->bc == LBM_BC_WALLS || s->forced || s->mrt || small_t_on(s); }
+// The staged kernel's force/MRT tile serves forced or MRT lattices that are
+// periodic, FP32 and without the small-T recovery.
+bool ext_ok(const lbm_sim* s) {
+    return (s->forced || s->mrt) && s->bc == LBM_BC_PERIODIC && s->dtype == DT_F32 && s->D >= 2 && !small_t_on(s) &&
+           s->opts.model == LBM_MODEL_BUMP && !s->opts.inplace;
+}
 bool variant_allowed(const lbm_sim* s, int v) {
+    if (v == kExtVariant) return ext_ok(s);
     if (!generic_only(s)) return true;
     return v < kTmaBase && !(s->D == 2 && v == 3);
 }
@@ -207,8 +214,12 @@ bool variant_allowed(const lbm_sim* s, int v) {
 // The TMA-staged kernel needs FP32/16-bit storage, tiles that divide the
 // extents, and rows whose byte length is a multiple of 16 (tensor strides).
 bool tma_applicable(const lbm_sim* s, int v) {
-    if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64 || generic_only(s)) return false;
-    if (v >= kPairBase) {
+    if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64) return false;
+    if (v == kExtVariant) {
+        if (!ext_ok(s)) return false;
+    } else if (generic_only(s)) {
+        return false;
+    } else if (v >= kPairBase) {
         // the pair kernel: FP32 storage, periodic lattices
         if (v - kPairBase >= n_pair_variants(s->D)) return false;
         if (s->dtype != DT_F32 || s->bc != LBM_BC_PERIODIC) return false;
@@ -581,8 +592,14 @@ lbm_status autotune(lbm_sim* s) {
         s->chunk = s->opts.chunk > 0 ? s->opts.chunk : 32;
         return ensure_partial(s, s->var, s->chunk);
     }
-    auto key = std::make_tuple(s->D, s->dtype * 2 + (generic_only(s) ? 1 : 0), s->nx, s->ny, s->nz);
-    {
+    // Lattices that share a result: same dimension, storage, extents,
+    // boundary and set of kernels that implement their settings (plain;
+    // force or MRT without walls; walls or the small-T recovery).  A forced
+    // tile or chunk is not looked up.
+    const int kernels = ext_ok(s) ? 2 : (generic_only(s) ? 1 : 0);
+    auto key = std::make_tuple(s->D, s->dtype * 3 + kernels, (int)s->bc, s->nx, s->ny, s->nz);
+    const bool forced_cfg = s->opts.tile >= 0 || s->opts.chunk > 0;
+    if (!forced_cfg) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
@@ -603,6 +620,7 @@ lbm_status autotune(lbm_sim* s) {
             if (tma_applicable(s, kTmaBase + k)) vars.push_back(kTmaBase + k);
         for (int k = 0; k < n_pair_variants(s->D); ++k)
             if (tma_applicable(s, kPairBase + k)) vars.push_back(kPairBase + k);
+        if (tma_applicable(s, kExtVariant)) vars.push_back(kExtVariant);
     }
     std::vector<int> chunks = s->opts.chunk > 0 ? std::vector<int>{s->opts.chunk} : chunk_candidates(s);
     if (vars.size() * chunks.size() == 1) {
@@ -651,7 +669,7 @@ lbm_status autotune(lbm_sim* s) {
     cudaEventDestroy(e1);
     s->var = bv;
     s->chunk = bc;
-    {
+    if (!forced_cfg) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune[key] = {bv, bc};
     }

@@ -1,21 +1,24 @@
 // Continuous-batching service (include/lbm_serve.h): many resident D1Q3 /
 // D2Q9 simulations in FP32 (1D fixed-state ones in FP64) advanced together by
-// one cooperative kernel.
+// one persistent cooperative kernel.
 //
-// Device side: serve_kernel walks a work list of tiles of every active
-// simulation -- 1D: 256-site strips run by the generic kernel's tile body
-// (step_block); 2D: strips of 254 sites x kChunk2 rows run by the strip
-// kernel's body (strip_block, any extent) -- with a grid-wide
-// barrier between steps; it advances the round's K steps in one launch.  Each
-// simulation keeps its own A-B buffers, parity and step budget for the round.
-//
-// A simulation that finishes within a round has its moments computed in the
-// same launch, after the last step (the tile body with the state update off).
+// Device side: serve_kernel stays resident and runs round after round.  A
+// round walks a work list of tiles of every active simulation -- 1D:
+// 256-site strips run by the generic kernel's tile body (step_block); 2D:
+// strips of 254 sites x kChunk2 rows run by the strip kernel's body
+// (strip_block, any extent) -- with a grid-wide barrier between its K steps.
+// Each simulation keeps its own A-B buffers, parity and step budget for the
+// round.  Admitted simulations get their start state in their first round;
+// a simulation that finishes within a round has its moments computed in the
+// same round, after the last step (the tile body with the state update off).
 //
 // Host side: a service thread admits queued requests first come first
-// served while their state fits the device pool and launches rounds.  The
-// loop is pipelined one round deep: round i is enqueued (admissions' field
-// copies and start kernels, the work list, the launch) before the thread
+// served while their state fits the device pool, copies their fields and
+// each round's work list to the device (copies only, on a second stream),
+// and posts the round in a mailbox in mapped host memory; block 0 of the
+// kernel polls it (bounded: the kernel leaves after an idle limit and is
+// launched again when work arrives) and reports each round done there.
+// The loop is pipelined one round deep: round i is posted before the thread
 // waits for round i - 1 and copies its finished simulations' moments out, so
 // the device never waits for the host's bookkeeping.
 #include <cooperative_groups.h>
@@ -55,6 +58,8 @@ constexpr size_t kAlign = 256;
 struct ServeSim {
     StepArgs a[2];  // per-simulation arguments for input buffer 0 and 1
     StepArgs am;    // moments of the state after the round (fin = 1): write_state 0, mout set
+    const double* m;  // init = 1: the start fields (rho, u, T) in device memory
+    int init;       // 1: admitted for this round; the round first computes its start state
     int fin;        // 1: the simulation finishes in this round
     void* f[2];
     void* b[2];
@@ -71,7 +76,10 @@ constexpr size_t kmax(size_t x, size_t y) { return x > y ? x : y; }
 constexpr size_t kSmem = kmax(kmax(Sh1::smem, Sh1d::smem), (size_t)ShS::SMEM);
 
 // One tile of simulation S with arguments a (a step, or the moments pass).
-__device__ __forceinline__ void serve_tile(const ServeSim& S, const StepArgs& a, int local, unsigned char* smem) {
+// A call, not inlined: inlined into the persistent loop, the tile bodies
+// lose registers to values the compiler keeps across rounds and spill; as a
+// function each has the whole register budget, for one call per work item.
+__device__ __noinline__ void serve_tile(const ServeSim& S, const StepArgs& a, int local, unsigned char* smem) {
     if (S.d == 1) {
         if (S.dt == DT_F64)
             step_block<1, double, kTX, 1>(a, local, 0, 0, smem);
@@ -90,7 +98,7 @@ __device__ __forceinline__ void serve_tile(const ServeSim& S, const StepArgs& a,
 }
 
 // The simulation that work item `it` belongs to: the last with item0 <= it.
-__device__ __forceinline__ int serve_owner(const ServeSim* __restrict__ sims, int nsims, int it) {
+__device__ __forceinline__ int serve_owner(const ServeSim* sims, int nsims, int it) {
     int lo = 0, hi = nsims - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -102,15 +110,95 @@ __device__ __forceinline__ int serve_owner(const ServeSim* __restrict__ sims, in
     return lo;
 }
 
+// Host <-> kernel mailbox in mapped pinned host memory.  The host posts
+// round number `post` after writing its descriptor (and after the round's
+// work list and admitted fields have reached device memory); the kernel
+// reports `done` after the round's last store.  Rounds are numbered from 1;
+// descriptor, timestamps and work list are double-buffered by round parity.
+struct RoundDesc {
+    int ns, items, K, ninit;
+};
+struct alignas(64) Mailbox {
+    long long post;   // host: last round posted
+    long long done;   // kernel: last round completed
+    int stop;         // host: 1 = leave at the next poll
+    int pad0;
+    long long pad[5];
+    RoundDesc desc[2];
+    unsigned long long t_start[2], t_end[2];  // %globaltimer at round start and end
+};
+// What block 0 read from the mailbox, for every block (device memory).
+struct RoundCtl {
+    int status, ns, items, K, ninit;
+};
+
+__device__ __forceinline__ long long ld_acquire_sys(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(long long* p, long long v) {
+    asm volatile("st.release.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long serve_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Start state of a simulation admitted for this round (grid-stride over its
+// sites and reservoir rows), as init_kernel / reservoir_kernel compute it.
+__device__ __noinline__ void serve_init(const ServeSim& S) {
+    const StepArgs& a = S.a[0];
+    const long long N = a.N, rows = a.rows;
+    const double* m = S.m;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, dt = (long long)gridDim.x * blockDim.x;
+    const double *rho = m, *u = m + N, *T = m + (1 + S.d) * N;
+    for (long long s = t0; s < N; s += dt) {
+        if (S.d == 1 && S.dt == DT_F64)
+            init_site<1, double>(rho, u, T, static_cast<double*>(S.f[0]), static_cast<double*>(S.b[0]), N, s);
+        else if (S.d == 1)
+            init_site<1, float>(rho, u, T, static_cast<float*>(S.f[0]), static_cast<float*>(S.b[0]), N, s);
+        else
+            init_site<2, float>(rho, u, T, static_cast<float*>(S.f[0]), static_cast<float*>(S.b[0]), N, s);
+    }
+    if (a.fixed_x)
+        for (long long t = t0; t < 2 * rows; t += dt) {
+            if (S.d == 1 && S.dt == DT_F64)
+                reservoir_item<1, double>(rho, u, T, a.nx, rows, N, static_cast<double*>(const_cast<void*>(a.gf)),
+                                          static_cast<double*>(const_cast<void*>(a.gb)), static_cast<double*>(const_cast<void*>(a.gaux)), t);
+            else if (S.d == 1)
+                reservoir_item<1, float>(rho, u, T, a.nx, rows, N, static_cast<float*>(const_cast<void*>(a.gf)),
+                                         static_cast<float*>(const_cast<void*>(a.gb)), static_cast<float*>(const_cast<void*>(a.gaux)), t);
+            else
+                reservoir_item<2, float>(rho, u, T, a.nx, rows, N, static_cast<float*>(const_cast<void*>(a.gf)),
+                                         static_cast<float*>(const_cast<void*>(a.gb)), static_cast<float*>(const_cast<void*>(a.gaux)), t);
+        }
+    if (t0 == 0) *a.flag = 0;
+}
+
 // K steps of every simulation in `sims` (sorted by item0), then the moments
 // of the simulations that finish in this round.
-__global__ void __launch_bounds__(kTX, 2) serve_kernel(const ServeSim* __restrict__ sims, int nsims, int nitems,
-                                                    int K) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    cg::grid_group grid = cg::this_grid();
-    for (int k = 0; k < K; ++k) {
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-            const ServeSim& S = sims[serve_owner(sims, nsims, it)];
+// The round's parameters (work list parity, simulations, work items, steps)
+// are read from shared memory where they are used: kept in registers across
+// the round, they would crowd the step bodies (128 registers a thread).
+struct RoundShared {
+    long long seq;
+    int ns, items, K;
+};
+
+__device__ __forceinline__ const ServeSim* round_sims(const ServeSim* tables, int max_active,
+                                                      const volatile RoundShared* r) {
+    return tables + (size_t)(r->seq & 1) * max_active;
+}
+
+__device__ __forceinline__ void serve_round(const ServeSim* tables, int max_active,
+                                            const volatile RoundShared* r, unsigned char* smem,
+                                            cg::grid_group& grid) {
+    for (int k = 0; k < r->K; ++k) {
+        for (int it = blockIdx.x; it < r->items; it += gridDim.x) {
+            const ServeSim* sims = round_sims(tables, max_active, r);
+            const ServeSim& S = sims[serve_owner(sims, r->ns, it)];
             if (k >= S.steps) continue;  // uniform over the block
             // read in place (not copied to registers): the tile bodies load
             // the fields they need
@@ -119,9 +207,88 @@ __global__ void __launch_bounds__(kTX, 2) serve_kernel(const ServeSim* __restric
         grid.sync();
     }
     // every step of the round is complete (the barrier above): moments
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const ServeSim& S = sims[serve_owner(sims, nsims, it)];
+    for (int it = blockIdx.x; it < r->items; it += gridDim.x) {
+        const ServeSim* sims = round_sims(tables, max_active, r);
+        const ServeSim& S = sims[serve_owner(sims, r->ns, it)];
         if (S.fin) serve_tile(S, S.am, it - S.item0, smem);
+    }
+}
+
+// The work lists are read with plain (coherent) loads, never through the
+// read-only path: the host rewrites a list between the rounds that use it.
+//
+// The persistent batched kernel: one cooperative launch serves round after
+// round.  Block 0 waits for the host to post the next round (bounded: after
+// idle_ns without a post, or when the host asks it to stop, every block
+// leaves together and the host relaunches when work arrives), then every
+// block runs it: start states of the admitted simulations, K steps of every
+// active simulation with a grid-wide barrier between steps, moments of the
+// finishing ones; block 0 then reports the round done.
+__global__ void __launch_bounds__(kTX, 2) serve_kernel(Mailbox* mb, RoundCtl* ctl, const ServeSim* tables,
+                                                    int max_active, long long seq0, unsigned long long idle_ns) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ RoundShared rs;
+    volatile RoundShared* r = &rs;
+    cg::grid_group grid = cg::this_grid();
+    volatile RoundCtl* vc = ctl;
+    if (threadIdx.x == 0) r->seq = seq0;
+    __syncthreads();
+    for (;;) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const long long seq = r->seq;
+            const int par = (int)(seq & 1);
+            int st = 0;
+            const unsigned long long t0 = serve_ns();
+            unsigned int nap = 128;
+            while (ld_acquire_sys(&mb->post) < seq) {
+                if (*(volatile int*)&mb->stop) {
+                    st = 2;
+                    break;
+                }
+                if (serve_ns() - t0 > idle_ns) {
+                    st = 1;
+                    break;
+                }
+                __nanosleep(nap);
+                if (nap < 4096) nap *= 2;
+            }
+            if (st == 0) {
+                const volatile RoundDesc* d = &mb->desc[par];
+                vc->ns = d->ns;
+                vc->items = d->items;
+                vc->K = d->K;
+                vc->ninit = d->ninit;
+                *(volatile unsigned long long*)&mb->t_start[par] = serve_ns();
+            }
+            vc->status = st;
+            __threadfence();
+        }
+        grid.sync();
+        if (vc->status != 0) return;  // every block leaves together
+        if (threadIdx.x == 0) {
+            r->ns = vc->ns;
+            r->items = vc->items;
+            r->K = vc->K;
+        }
+        __syncthreads();
+        if (vc->ninit > 0) {
+            const ServeSim* sims = round_sims(tables, max_active, r);
+            for (int i = 0; i < r->ns; ++i)
+                if (sims[i].init) serve_init(sims[i]);
+            grid.sync();
+        }
+        serve_round(tables, max_active, r, smem, grid);
+        grid.sync();
+        if (threadIdx.x == 0) {
+            const long long seq = r->seq;
+            if (blockIdx.x == 0) {
+                *(volatile unsigned long long*)&mb->t_end[seq & 1] = serve_ns();
+                __threadfence_system();
+                st_release_sys(&mb->done, seq);
+            }
+            r->seq = seq + 1;  // every thread of the block has passed its last read (barriers above)
+        }
+        __syncthreads();
     }
 }
 
@@ -222,6 +389,7 @@ struct Request {
     int state = 0;  // 0 queued, 1 active, 2 done
     int flag = 0;
     int cur = 0;
+    bool fresh = false;  // admitted; its start state is computed by its first round
     int dt = DT_F32;
     size_t off = 0;
     Layout lay{};
@@ -241,14 +409,19 @@ int request_dtype(int d, lbm_bc bc) { return (d == 1 && bc == LBM_BC_FIXED_STATE
 struct Server {
     lbm_server_opts opts{};
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // the persistent kernel
     char* pool_mem = nullptr;
     Pool pool;
-    cudaStream_t cstream = nullptr;  // copies of finished simulations' moments
+    cudaStream_t cstream = nullptr;  // copies: admitted fields and work lists in, results out
     ServeSim* d_sims = nullptr;      // [2][max_active]: work lists of rounds i and i + 1
     ServeSim* h_sims = nullptr;      // pinned, [2][max_active]
     int* h_flag = nullptr;           // pinned
-    cudaEvent_t ev0[2] = {nullptr, nullptr}, ev1[2] = {nullptr, nullptr};
+    Mailbox* mb = nullptr;           // pinned, mapped: host view
+    Mailbox* mb_dev = nullptr;       // device view of the same memory
+    RoundCtl* ctl = nullptr;         // device
+    bool launched = false;           // a launch of the persistent kernel was made on `stream`
+    long long posted = 0;            // rounds posted so far
+    uint64_t launches = 0;
     double* stage[2] = {nullptr, nullptr};  // pinned staging of admitted fields, per round parity
     size_t stage_n[2] = {0, 0};             // doubles
     int grid_max = 0;
@@ -274,7 +447,53 @@ struct Server {
     void loop();
     bool admit_one(const std::shared_ptr<Request>& r, double* staged);
     bool finish(std::vector<std::shared_ptr<Request>>& done, int par, int nsims);
+    bool ensure_kernel();
+    bool wait_done(long long seq);
+    bool fail_thread(const std::string& m) {
+        std::lock_guard<std::mutex> lk(mu);
+        thread_error = m;
+        cv_done.notify_all();
+        return false;
+    }
 };
+
+long long host_load_acquire(const long long* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+void host_store_release(long long* p, long long v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+
+// The persistent kernel runs on `stream` unless it has left (idle limit or
+// stop); then it is launched again, starting at the first round not done.
+bool Server::ensure_kernel() {
+    if (launched) {
+        const cudaError_t q = cudaStreamQuery(stream);
+        if (q == cudaErrorNotReady) return true;  // still running
+        if (q != cudaSuccess) return fail_thread(std::string("serve kernel: ") + cudaGetErrorString(q));
+    }
+    *(volatile int*)&mb->stop = 0;
+    long long seq0 = host_load_acquire(&mb->done) + 1;
+    unsigned long long idle_ns = (unsigned long long)(opts.idle_ms * 1e6);
+    int ma = opts.max_active;
+    void* args[] = {&mb_dev, &ctl, &d_sims, &ma, &seq0, &idle_ns};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)serve_kernel, dim3(grid_max), dim3(kTX), args, kSmem,
+                                                stream);
+    if (e != cudaSuccess) return fail_thread(std::string("serve kernel launch: ") + cudaGetErrorString(e));
+    launched = true;
+    ++launches;
+    return true;
+}
+
+// Wait until round `seq` is done; relaunch the kernel if it left first.
+bool Server::wait_done(long long seq) {
+    const auto t_start = std::chrono::steady_clock::now();
+    unsigned int nap = 2;
+    while (host_load_acquire(&mb->done) < seq) {
+        if (!ensure_kernel()) return false;
+        if (std::chrono::steady_clock::now() - t_start > std::chrono::seconds(600))
+            return fail_thread("serve kernel: a round did not complete within 600 s");
+        std::this_thread::sleep_for(std::chrono::microseconds(nap));
+        if (nap < 200) nap *= 2;
+    }
+    return true;
+}
 
 // 2D requests run on the strip kernel's tile body.
 bool uses_strip(const Request& r) { return r.d == 2; }
@@ -310,22 +529,12 @@ bool Server::admit_one(const std::shared_ptr<Request>& r, double* staged) {
     char* base = pool_mem + r->off;
     double* m = reinterpret_cast<double*>(base + r->lay.m);
     const long long N = r->N;
-    cudaError_t e = cudaMemcpyAsync(m, staged, sizeof(double) * (2 + r->d) * N, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + r->lay.flag, 0, sizeof(int), stream);
-    if (e == cudaSuccess)
-        e = launch_init(r->d, r->dt, m, m + N, m + (1 + r->d) * N, base + r->lay.f[0], base + r->lay.b[0], N,
-                        stream);
-    if (e == cudaSuccess && r->bc == LBM_BC_FIXED_STATE)
-        e = launch_reservoir(r->d, r->dt, m, m + N, m + (1 + r->d) * N, r->nx, r->ny, N, base + r->lay.gf,
-                             base + r->lay.gb, base + r->lay.gaux, stream);
-    if (e != cudaSuccess) {
-        std::lock_guard<std::mutex> lk(mu);
-        thread_error = std::string("admission: ") + cudaGetErrorString(e);
-        cv_done.notify_all();
-        return false;
-    }
+    // a copy only: no kernel may queue behind the persistent one
+    cudaError_t e = cudaMemcpyAsync(m, staged, sizeof(double) * (2 + r->d) * N, cudaMemcpyHostToDevice, cstream);
+    if (e != cudaSuccess) return fail_thread(std::string("admission: ") + cudaGetErrorString(e));
     r->cur = 0;
     r->remaining = r->steps;
+    r->fresh = true;
     return true;
 }
 
@@ -333,8 +542,9 @@ bool Server::admit_one(const std::shared_ptr<Request>& r, double* staged) {
 // event): its time, and the results of the simulations that finished in it
 // (moments computed by the round itself) copied to their host vectors.
 bool Server::finish(std::vector<std::shared_ptr<Request>>& done, int par, int nsims) {
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ev0[par], ev1[par]);
+    const unsigned long long te = *(volatile unsigned long long*)&mb->t_end[par];
+    const unsigned long long ts = *(volatile unsigned long long*)&mb->t_start[par];
+    const double ms = te > ts ? (te - ts) * 1e-6 : 0.0;
     double done_sites = 0;
     const ServeSim* hs = h_sims + (size_t)par * opts.max_active;
     for (int i = 0; i < nsims; ++i) done_sites += (double)hs[i].a[0].N * hs[i].steps;
@@ -373,10 +583,9 @@ bool Server::finish(std::vector<std::shared_ptr<Request>>& done, int par, int ns
 
 void Server::loop() {
     cudaSetDevice(device);
-    int par = 0;                 // parity of the round being enqueued
-    bool inflight = false;       // round 1 - par is on the device
+    bool inflight = false;       // round `posted` is on the device
     int inflight_n = 0;          // its number of simulations
-    std::vector<std::shared_ptr<Request>> fin[2];  // simulations that finish in round par
+    std::vector<std::shared_ptr<Request>> fin[2];  // simulations that finish in the round of that parity
     while (true) {
         std::vector<std::shared_ptr<Request>> admitted;
         bool stopping = false;
@@ -397,9 +606,15 @@ void Server::loop() {
             }
         }
         if (stopping) {
-            cudaStreamSynchronize(stream);  // nothing of the server in flight on return
+            // the kernel leaves at its next poll; nothing of the server in
+            // flight on return
+            *(volatile int*)&mb->stop = 1;
+            cudaStreamSynchronize(stream);
+            cudaStreamSynchronize(cstream);
             return;
         }
+        const long long seq = posted + 1;
+        const int par = (int)(seq & 1);
         // admissions: fields into this parity's pinned staging (its last
         // copies, two rounds ago, have completed), then onto the device
         if (!admitted.empty()) {
@@ -410,9 +625,7 @@ void Server::loop() {
                 stage[par] = nullptr;
                 stage_n[par] = 0;
                 if (cudaMallocHost(&stage[par], sizeof(double) * need) != cudaSuccess) {
-                    std::lock_guard<std::mutex> lk(mu);
-                    thread_error = "admission: pinned staging memory";
-                    cv_done.notify_all();
+                    fail_thread("admission: pinned staging memory");
                     return;
                 }
                 stage_n[par] = need;
@@ -427,9 +640,9 @@ void Server::loop() {
             }
         }
 
-        // round i: every active simulation advances min(K, remaining) steps;
-        // the host's copy of each simulation's step count and parity moves
-        // ahead at once (the device follows in stream order)
+        // round `seq`: every active simulation advances min(K, remaining)
+        // steps; the host's copy of each simulation's step count and parity
+        // moves ahead at once (the device follows in round order)
         int ns = (int)active.size();
         fin[par].clear();
         if (ns > 0) {
@@ -443,7 +656,7 @@ void Server::loop() {
             K = std::max(1L, std::min({K, max_rem, 4096L}));
             ServeSim* hs = h_sims + (size_t)par * opts.max_active;
             ServeSim* ds = d_sims + (size_t)par * opts.max_active;
-            int items = 0;
+            int items = 0, ninit = 0;
             std::vector<std::shared_ptr<Request>> still;
             for (int i = 0; i < ns; ++i) {
                 const auto& rp = active[i];
@@ -461,6 +674,10 @@ void Server::loop() {
                     sm.a[k].fout = sm.f[k ^ 1];
                     sm.a[k].bout = sm.b[k ^ 1];
                 }
+                sm.m = reinterpret_cast<const double*>(base + r.lay.m);
+                sm.init = r.fresh ? 1 : 0;
+                ninit += sm.init;
+                rp->fresh = false;
                 sm.d = r.d;
                 sm.dt = r.dt;
                 sm.strip = uses_strip(r) ? 1 : 0;
@@ -484,38 +701,34 @@ void Server::loop() {
                 else
                     still.push_back(rp);
             }
-            cudaError_t e = cudaMemcpyAsync(ds, hs, sizeof(ServeSim) * ns, cudaMemcpyHostToDevice, stream);
-            int grid = std::max(1, std::min(grid_max, items));
-            int Ki = (int)K;
-            void* args[] = {&ds, (void*)&ns, &items, &Ki};
-            if (e == cudaSuccess) e = cudaEventRecord(ev0[par], stream);
-            if (e == cudaSuccess)
-                e = cudaLaunchCooperativeKernel((const void*)serve_kernel, dim3(grid), dim3(kTX), args, kSmem, stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev1[par], stream);
+            // the work list and the admitted fields reach device memory
+            // before the round is posted
+            cudaError_t e = cudaMemcpyAsync(ds, hs, sizeof(ServeSim) * ns, cudaMemcpyHostToDevice, cstream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cstream);
             if (e != cudaSuccess) {
-                std::lock_guard<std::mutex> lk(mu);
-                thread_error = std::string("round: ") + cudaGetErrorString(e);
-                cv_done.notify_all();
+                fail_thread(std::string("round: ") + cudaGetErrorString(e));
                 return;
             }
+            volatile RoundDesc* d = &mb->desc[par];
+            d->ns = ns;
+            d->items = items;
+            d->K = (int)K;
+            d->ninit = ninit;
+            host_store_release(&mb->post, seq);
+            posted = seq;
+            if (!ensure_kernel()) return;
             active.swap(still);
         }
 
-        // round i - 1: wait for it (round i is queued behind it), then its
-        // results
+        // round seq - 1: wait for it (round seq is posted behind it), then
+        // its results
         if (inflight) {
-            if (cudaEventSynchronize(ev1[par ^ 1]) != cudaSuccess) {
-                std::lock_guard<std::mutex> lk(mu);
-                thread_error = "round: the batched launch failed";
-                cv_done.notify_all();
-                return;
-            }
+            if (!wait_done(seq - 1)) return;
             if (!finish(fin[par ^ 1], par ^ 1, inflight_n)) return;
             fin[par ^ 1].clear();
         }
         inflight = ns > 0;
         inflight_n = ns;
-        if (ns > 0) par ^= 1;
     }
 }
 
@@ -559,6 +772,7 @@ void lbm_server_default_opts(lbm_server_opts* o) {
     o->max_active = 4096;
     o->device = 0;
     o->round_ms = 2.0;
+    o->idle_ms = 50.0;
 }
 
 lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
@@ -569,6 +783,7 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
     if (opts) o = *opts;
     if (o.max_active <= 0) o.max_active = 4096;
     if (!(o.round_ms > 0)) o.round_ms = 2.0;
+    if (!(o.idle_ms > 0)) o.idle_ms = 50.0;
     auto* h = new lbm_server();
     Server& S = h->s;
     S.opts = o;
@@ -579,10 +794,8 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         if (S.pool_mem) cudaFree(S.pool_mem);
         if (S.h_sims) cudaFreeHost(S.h_sims);
         if (S.h_flag) cudaFreeHost(S.h_flag);
-        for (int k = 0; k < 2; ++k) {
-            if (S.ev0[k]) cudaEventDestroy(S.ev0[k]);
-            if (S.ev1[k]) cudaEventDestroy(S.ev1[k]);
-        }
+        if (S.mb) cudaFreeHost(S.mb);
+        if (S.ctl) cudaFree(S.ctl);
         if (S.stream) cudaStreamDestroy(S.stream);
         if (S.cstream) cudaStreamDestroy(S.cstream);
         delete h;
@@ -601,9 +814,11 @@ lbm_status lbm_server_create(const lbm_server_opts* opts, lbm_server** out) {
         (e = cudaMalloc(&S.d_sims, 2 * sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
         (e = cudaMallocHost(&S.h_sims, 2 * sizeof(ServeSim) * o.max_active)) != cudaSuccess ||
         (e = cudaMallocHost(&S.h_flag, sizeof(int))) != cudaSuccess ||
-        (e = cudaEventCreate(&S.ev0[0])) != cudaSuccess || (e = cudaEventCreate(&S.ev1[0])) != cudaSuccess ||
-        (e = cudaEventCreate(&S.ev0[1])) != cudaSuccess || (e = cudaEventCreate(&S.ev1[1])) != cudaSuccess)
+        (e = cudaHostAlloc(&S.mb, sizeof(Mailbox), cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer((void**)&S.mb_dev, S.mb, 0)) != cudaSuccess ||
+        (e = cudaMalloc(&S.ctl, sizeof(RoundCtl))) != cudaSuccess)
         return cleanup(std::string("server set-up: ") + cudaGetErrorString(e));
+    std::memset(S.mb, 0, sizeof(Mailbox));
     S.pool.reset(S.pool_mem, o.hbm_budget);
     int per_sm = 0, sms = 0;
     // the strip body needs more than the default 48 KB of dynamic shared memory
@@ -699,6 +914,7 @@ lbm_status lbm_server_stats_get(lbm_server* h, lbm_server_stats* o) {
     o->last_done_s = S.last_done;
     o->pool_bytes = S.pool.size;
     o->pool_in_use = S.pool.in_use;
+    o->kernel_launches = S.launches;
     return LBM_OK;
 }
 
@@ -711,17 +927,19 @@ void lbm_server_destroy(lbm_server* h) {
     }
     S.cv_work.notify_all();
     if (S.worker.joinable()) S.worker.join();
+    // the persistent kernel leaves at its next poll (the worker may have
+    // returned on an error without asking it to)
+    *(volatile int*)&S.mb->stop = 1;
     cudaStreamSynchronize(S.stream);
     cudaStreamSynchronize(S.cstream);
     cudaFree(S.d_sims);
     cudaFree(S.pool_mem);
+    cudaFree(S.ctl);
     cudaFreeHost(S.h_sims);
     cudaFreeHost(S.h_flag);
-    for (int k = 0; k < 2; ++k) {
-        cudaEventDestroy(S.ev0[k]);
-        cudaEventDestroy(S.ev1[k]);
+    cudaFreeHost(S.mb);
+    for (int k = 0; k < 2; ++k)
         if (S.stage[k]) cudaFreeHost(S.stage[k]);
-    }
     cudaStreamDestroy(S.stream);
     cudaStreamDestroy(S.cstream);
     delete h;

@@ -42,6 +42,7 @@
 #include <utility>
 
 #include "lbm_lean.cuh"
+#include "lbm_mrt.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
@@ -50,12 +51,16 @@ namespace lbm {
 // its pulled populations to stage 2 through shared memory instead of pulling
 // them a second time; bit 2 (with bit 1) -- those populations and the site
 // values live in tensor memory (TMEM) instead of shared memory, so that more
-// blocks fit per SM.  MB: resident blocks per SM the launch bounds aim at.
+// blocks fit per SM; bit 3 -- stage 2 also applies a uniform body force
+// (StepArgs::forced) and, on D3Q19, the MRT collision (StepArgs::mrt), as
+// the generic kernel does.  MB: resident blocks per SM the launch bounds aim
+// at.
 template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape {
     using L = Lattice<D>;
     static constexpr int PF = PFB & 1;
     static constexpr bool DFS = (PFB & 2) != 0;
     static constexpr bool TM = (PFB & 4) != 0;
+    static constexpr bool EXT = (PFB & 8) != 0;
     static constexpr int Q = L::Q, NB = L::NB;
     static constexpr int PXB = 4;                                   // 16-byte aligned x start of a b copy
     static constexpr int SXB = TX + 2 * PXB;                        // sites per staged row
@@ -470,7 +475,28 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
                 pull(p, zsp, df);  // second pull of the same values
             }
         }
+        if constexpr (Sh::EXT) {
+            if (a.forced) {
+                // body force: F + rho a, G + (rho u a + a rho u) with the
+                // corrected momentum rho u = j0 + F/2 (Eq. 57)
+                float ga[D], ru[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    ga[c] = acc_param(a, c, 0.0f);
+                    F[c] += c_rho * ga[c];
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) ru[c] = c_j[c] + 0.5f * F[c];
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+#pragma unroll
+                    for (int d2 = c; d2 < D; ++d2) G[sym<D>(c, d2)] += ru[c] * ga[d2] + ru[d2] * ga[c];
+            }
+        }
         site_collide<D, FS, float, int, DiagDev<D + 2>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
+        if constexpr (Sh::EXT && D == 3) {
+            if (a.mrt && a.write_state) mrt_correct<FS, float>(a, s, df, c_rho, c_j, F);
+        }
     }
 };
 

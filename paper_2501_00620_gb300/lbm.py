@@ -73,7 +73,8 @@ class lbm_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t),
                 ("max_active", ctypes.c_int),
                 ("device", ctypes.c_int),
-                ("round_ms", ctypes.c_double)]
+                ("round_ms", ctypes.c_double),
+                ("idle_ms", ctypes.c_double)]
 
 
 class lbm_request(ctypes.Structure):
@@ -101,7 +102,8 @@ class lbm_server_stats(ctypes.Structure):
                 ("first_submit_s", ctypes.c_double),
                 ("last_done_s", ctypes.c_double),
                 ("pool_bytes", ctypes.c_size_t),
-                ("pool_in_use", ctypes.c_size_t)]
+                ("pool_in_use", ctypes.c_size_t),
+                ("kernel_launches", ctypes.c_uint64)]
 
 
 def _load():
@@ -515,7 +517,7 @@ class ServeResult(tuple):
 class Server:
     """Continuous-batching service for D1Q3 / D2Q9 requests (FP32)."""
 
-    def __init__(self, hbm_budget=0, max_active=0, device=0, round_ms=0.0):
+    def __init__(self, hbm_budget=0, max_active=0, device=0, round_ms=0.0, idle_ms=0.0):
         o = lbm_server_default_opts()
         o.hbm_budget = int(hbm_budget)
         if max_active:
@@ -523,6 +525,8 @@ class Server:
         o.device = device
         if round_ms:
             o.round_ms = float(round_ms)
+        if idle_ms:
+            o.idle_ms = float(idle_ms)
         h = ctypes.c_void_p()
         _check(_lib.lbm_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.h = h

@@ -136,25 +136,63 @@ def test_poiseuille_fp32_matches_oracle_viscosity():
     assert np.abs(u[0] - u[0][:, :, :1]).max() < 1e-6 * np.abs(u[0]).max() + 1e-9
 
 
-def test_force_switches_to_generic_kernel():
-    """A forced or walled lattice runs on the generic kernel: setting a force
-    on a tuned periodic FP32 lattice re-tunes among the kernels that
-    implement it, and the momentum then grows by M a per step."""
+def test_force_switches_to_kernels_with_the_force():
+    """A forced lattice runs on a kernel that implements the force: setting a
+    force on a tuned periodic FP32 lattice re-tunes among the generic kernel
+    and the staged kernel's force/MRT tile, and the momentum then grows by
+    M a per step; a walled lattice runs on the generic kernel."""
     n = 64
     g = lbm.Simulation(3, n, n, n, tau=0.6, T0=0.1, dtype="f32")
     g.init(1.0, np.zeros((3, n, n, n)), 0.1)
     g.step(2)
+    assert g.launch_config()[0] != EXT_TILE
     acc = np.array([1e-4, 0.0, -2e-4])
     g.set_force(acc)
     d0 = g.diagnostics()
     g.step(10)
-    assert g.launch_config()[2] == "step_kernel"
+    tile, _, kernel = g.launch_config()
+    assert kernel == "step_kernel" or tile == EXT_TILE
     d1 = g.diagnostics()
     assert np.allclose((d1[1:4] - d0[1:4]) / (10 * d0[0]), acc, rtol=1e-4, atol=1e-9)
     w = lbm.Simulation(2, 256, 64, tau=0.6, T0=0.1, bc="walls", dtype="f32")
     w.init(1.0, np.zeros((2, 1, 64, 256)), 0.1)
     w.step(1)
     assert w.launch_config()[2] == "step_kernel"
+
+
+EXT_TILE = 150  # the staged kernel's force/MRT tile
+
+
+@pytest.mark.parametrize("d,shape", [(3, (20, 32, 64)), (3, (9, 16, 96)), (2, (1, 40, 256)), (2, (1, 17, 384))])
+def test_staged_force_tile_matches_generic_and_oracle(d, shape):
+    """The staged kernel's force/MRT tile with a body force: equal to the
+    generic kernel up to FP32 rounding after several steps (chunk lengths
+    that do and do not divide the march), and one step from an identical
+    state equal to the FP64 oracle to the FP32 storage precision."""
+    nz, ny, nx = shape
+    rho, u, T = random_fields(d, shape, 31, 0.1)
+    acc = [2e-4, -1e-4, 5e-5][:d]
+    ref = lbm.Simulation(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True, dtype="f32", tile=0, chunk=4)
+    ref.set_force(acc)
+    ref.init(rho, u, T)
+    ref.step(7)
+    fr, br = ref.emitted()
+    for chunk in (3, 8):
+        g = lbm.Simulation(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True, dtype="f32", tile=EXT_TILE, chunk=chunk)
+        g.set_force(acc)
+        g.init(rho, u, T)
+        g.step(6)
+        assert g.launch_config()[0] == EXT_TILE
+        f0, b0 = g.emitted()
+        g.step(1)
+        f1, b1 = g.emitted()
+        assert normwise(f1, fr) < 2e-5 and np.abs(b1 - br).max() < 2e-5
+        o = oracle.Sim(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True)
+        o.set_force(acc)
+        o.set_emitted(f0, b0)
+        o.step(1)
+        of, ob = o.emitted()
+        assert normwise(f1, of) < 2e-6 and np.abs(b1 - ob).max() < 2e-6
 
 
 @pytest.mark.parametrize("d,shape", [(2, (1, 23, 70)), (3, (13, 11, 37))])

@@ -12,6 +12,8 @@
   longest ones of the seeded mix stay physical and match the oracle.
 * Admission respects the device-memory budget: requests wait for room and
   the pool is empty again at the end.
+* The persistent kernel's waits are bounded: it leaves when idle and is
+  launched again when work arrives.
 """
 import time
 
@@ -188,4 +190,36 @@ def test_invalid_requests_are_refused():
             srv.submit(dim, nx, ny, 0.8, 0.3, False, "periodic", 10, np.ones(n), np.zeros(dim * n),
                        np.full(n, 0.3))
         assert e.value.status == lbm.LBM_EINVAL
+    srv.close()
+
+
+def test_persistent_kernel_leaves_when_idle_and_is_launched_again():
+    """The persistent kernel's wait for the next round is bounded: after
+    idle_ms without a posted round it leaves (no GPU time is held by an idle
+    server), the next request launches it again, and results do not depend
+    on which launch computed them; closing a server whose kernel is waiting
+    returns promptly."""
+    srv = lbm.Server(hbm_budget=1 << 28, idle_ms=20.0)
+    first = srv.wait(submit(srv, MIX[2]))
+    n1 = srv.stats()["kernel_launches"]
+    assert n1 >= 1
+    # several requests back to back share one launch
+    tickets = [submit(srv, req) for req in MIX[:4]]
+    for t in tickets:
+        srv.wait(t)
+    time.sleep(0.3)  # far past the idle limit: the kernel has left
+    n2 = srv.stats()["kernel_launches"]
+    again = srv.wait(submit(srv, MIX[2]))
+    assert srv.stats()["kernel_launches"] == n2 + 1
+    for x, y in zip(first[:3], again[:3]):
+        assert np.array_equal(x, y)
+    # a request submitted while the kernel waits joins without a new launch
+    srv2 = lbm.Server(hbm_budget=1 << 28, idle_ms=2000.0)
+    srv2.wait(submit(srv2, MIX[0]))
+    n = srv2.stats()["kernel_launches"]
+    srv2.wait(submit(srv2, MIX[0]))
+    assert srv2.stats()["kernel_launches"] == n
+    t0 = time.perf_counter()
+    srv2.close()  # the kernel is waiting for a round: the stop request ends it
+    assert time.perf_counter() - t0 < 1.5
     srv.close()
