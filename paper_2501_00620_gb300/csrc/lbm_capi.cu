@@ -205,8 +205,11 @@ bool ext_ok(const lbm_sim* s) {
     return (s->forced || s->mrt) && s->bc == LBM_BC_PERIODIC && s->dtype == DT_F32 && s->D >= 2 && !small_t_on(s) &&
            s->opts.model == LBM_MODEL_BUMP && !s->opts.inplace;
 }
+bool is_ext_variant(const lbm_sim* s, int v) {
+    return v >= kOwnBase && v < kOwnBase + n_own_variants(s->D) && own_is_ext(s->D, v - kOwnBase);
+}
 bool variant_allowed(const lbm_sim* s, int v) {
-    if (v == kExtVariant) return ext_ok(s);
+    if (is_ext_variant(s, v)) return ext_ok(s);
     if (!generic_only(s)) return true;
     return v < kTmaBase && !(s->D == 2 && v == 3);
 }
@@ -215,8 +218,11 @@ bool variant_allowed(const lbm_sim* s, int v) {
 // extents, and rows whose byte length is a multiple of 16 (tensor strides).
 bool tma_applicable(const lbm_sim* s, int v) {
     if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64) return false;
-    if (v == kExtVariant) {
-        if (!ext_ok(s)) return false;
+    if (v >= kOwnBase && v < kPairBase) {
+        // FP32, periodic-only tiles: the force/MRT tile for forced or MRT
+        // lattices, the others for plain ones
+        if (v >= kOwnBase + n_own_variants(s->D) || s->dtype != DT_F32 || s->bc != LBM_BC_PERIODIC) return false;
+        if (is_ext_variant(s, v) ? !ext_ok(s) : generic_only(s)) return false;
     } else if (generic_only(s)) {
         return false;
     } else if (v >= kPairBase) {
@@ -620,7 +626,8 @@ lbm_status autotune(lbm_sim* s) {
             if (tma_applicable(s, kTmaBase + k)) vars.push_back(kTmaBase + k);
         for (int k = 0; k < n_pair_variants(s->D); ++k)
             if (tma_applicable(s, kPairBase + k)) vars.push_back(kPairBase + k);
-        if (tma_applicable(s, kExtVariant)) vars.push_back(kExtVariant);
+        for (int k = 0; k < n_own_variants(s->D); ++k)
+            if (tma_applicable(s, kOwnBase + k)) vars.push_back(kOwnBase + k);
     }
     std::vector<int> chunks = s->opts.chunk > 0 ? std::vector<int>{s->opts.chunk} : chunk_candidates(s);
     if (vars.size() * chunks.size() == 1) {

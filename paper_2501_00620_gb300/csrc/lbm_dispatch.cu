@@ -55,7 +55,7 @@ int n_tma_variants(int D) { return D == 2 ? n_fast_variants_d2() : (D == 3 ? n_f
 int n_pair_variants(int D) { return D == 2 ? n_pair_variants_d2() : (D == 3 ? n_pair_variants_d3() : 0); }
 
 Variant variant(int D, int v) {
-    if (v == kExtVariant) return D == 3 ? Variant{32, 4} : (D == 2 ? Variant{128, 1} : Variant{0, 0});
+    if (v >= kOwnBase && v < kOwnBase + n_own_variants(D)) return own_variant(D, v - kOwnBase);
     if (v >= kPairBase && v < kStdVariant) {
         const int k = v - kPairBase;
         return D == 2 ? pair_variant_d2(k) : (D == 3 ? pair_variant_d3(k) : Variant{0, 0});
@@ -68,7 +68,9 @@ Variant variant(int D, int v) {
 }
 
 cudaError_t tma_box(int D, int dtype, int v, TmaBox* box) {
-    if (v == kExtVariant) return dtype == DT_F32 ? fast_ext_box(D, box) : cudaErrorInvalidValue;
+    if (v >= kOwnBase && v < kPairBase)
+        return dtype == DT_F32 && v < kOwnBase + n_own_variants(D) ? fast_own(D, v - kOwnBase, nullptr, box, nullptr)
+                                                                    : cudaErrorInvalidValue;
     if (v >= kPairBase) {
         const int kk = v - kPairBase;
         return D == 2 ? pair_box_d2(dtype, kk, box) : (D == 3 ? pair_box_d3(dtype, kk, box) : cudaErrorInvalidValue);
@@ -86,7 +88,9 @@ size_t step_smem(int D, int dtype, int v) {
 }
 
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st) {
-    if (v == kExtVariant) return dtype == DT_F32 ? launch_step_fast_ext(D, ta, st) : cudaErrorInvalidValue;
+    if (v >= kOwnBase && v < kPairBase)
+        return dtype == DT_F32 && v < kOwnBase + n_own_variants(D) ? fast_own(D, v - kOwnBase, &ta, nullptr, st)
+                                                                    : cudaErrorInvalidValue;
     if (v >= kPairBase) {
         const int kk = v - kPairBase;
         return D == 2 ? launch_step_pair_d2(dtype, kk, ta, st)

@@ -23,10 +23,11 @@ constexpr int kStripNT = 256;
 // kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;
 
-// The staged kernel's tile with the body-force and MRT terms in stage 2
-// (lbm_kernels_fastx.cu): FP32 storage, periodic lattices with a body force
-// or (D3Q19) the MRT collision.
-constexpr int kExtVariant = 150;
+// kOwnBase + k selects the k-th FP32, periodic-only tile of the staged
+// kernel (lbm_kernels_fastx.cu); k = 0 is the tile with the body-force and
+// MRT terms in stage 2, for lattices with a body force or (D3Q19) the MRT
+// collision.
+constexpr int kOwnBase = 150;
 
 // kPairBase + k selects the k-th tile of the pair kernel (lbm_step_pair.cuh):
 // FP32 storage, periodic lattices.
@@ -65,8 +66,10 @@ cudaError_t launch_step(int D, int dtype, int v, const StepArgs& a, cudaStream_t
 cudaError_t launch_step_multi_d1(int dtype, int v, const StepArgs& a0, const StepArgs& a1, int K,
                                  cudaStream_t st);
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st);
-cudaError_t fast_ext_box(int D, TmaBox* box);
-cudaError_t launch_step_fast_ext(int D, const TmaArgs& ta, cudaStream_t st);
+int n_own_variants(int D);
+Variant own_variant(int D, int k);
+bool own_is_ext(int D, int k);
+cudaError_t fast_own(int D, int k, const TmaArgs* ta, TmaBox* box, cudaStream_t st);
 // K steps of a small D2 lattice in one cooperative launch (the generic
 // kernel's strips of kMultiTX2 sites, a0.chunk rows per block).
 constexpr int kMultiTX2 = 128;

@@ -1,26 +1,44 @@
-// Launchers of the staged step kernel with the body-force and MRT terms in
-// stage 2 (kFastExt2, kFastExt3): FP32 storage, periodic lattices.
+// Launchers of the staged step kernel's FP32, periodic-only tiles (kFastOwn3,
+// kFastOwn2): the force/MRT tiles.
 #include "lbm_fast_launch.cuh"
 
 namespace lbm {
 
-cudaError_t fast_ext_box(int D, TmaBox* box) {
+int n_own_variants(int D) {
+    return D == 3 ? (int)(sizeof(kFastOwn3) / sizeof(kFastOwn3[0]))
+                  : (D == 2 ? (int)(sizeof(kFastOwn2) / sizeof(kFastOwn2[0])) : 0);
+}
+Variant own_variant(int D, int k) {
+    return D == 3 ? Variant{kFastOwn3[k].tx, kFastOwn3[k].ty} : Variant{kFastOwn2[k].tx, kFastOwn2[k].ty};
+}
+bool own_is_ext(int D, int k) { return ((D == 3 ? kFastOwn3[k].pfb : kFastOwn2[k].pfb) & 8) != 0; }
+
+#define LBM_OWN_CASE(DD, TAB, K)                                                                      \
+    case K:                                                                                           \
+        if (box) {                                                                                    \
+            fast_box<DD, float, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb>(box);                    \
+            return cudaSuccess;                                                                       \
+        }                                                                                             \
+        return launch_fast<DD, float, TAB[K].tx, TAB[K].ty, TAB[K].pfb, TAB[K].mb, false>(*ta, st);
+
+cudaError_t fast_own(int D, int k, const TmaArgs* ta, TmaBox* box, cudaStream_t st) {
+    if (ta && ta->s.fixed_x) return cudaErrorInvalidValue;
     if (D == 3) {
-        fast_box<3, float, kFastExt3.tx, kFastExt3.ty, kFastExt3.pfb, kFastExt3.mb>(box);
-        return cudaSuccess;
+        static_assert(sizeof(kFastOwn3) / sizeof(kFastOwn3[0]) == 1, "one case per tile");
+        switch (k) {
+            LBM_OWN_CASE(3, kFastOwn3, 0)
+            default: return cudaErrorInvalidValue;
+        }
     }
     if (D == 2) {
-        fast_box<2, float, kFastExt2.tx, kFastExt2.ty, kFastExt2.pfb, kFastExt2.mb>(box);
-        return cudaSuccess;
+        static_assert(sizeof(kFastOwn2) / sizeof(kFastOwn2[0]) == 1, "one case per tile");
+        switch (k) {
+            LBM_OWN_CASE(2, kFastOwn2, 0)
+            default: return cudaErrorInvalidValue;
+        }
     }
     return cudaErrorInvalidValue;
 }
-
-cudaError_t launch_step_fast_ext(int D, const TmaArgs& ta, cudaStream_t st) {
-    if (ta.s.fixed_x) return cudaErrorInvalidValue;
-    if (D == 3) return launch_fast<3, float, kFastExt3.tx, kFastExt3.ty, kFastExt3.pfb, kFastExt3.mb, false>(ta, st);
-    if (D == 2) return launch_fast<2, float, kFastExt2.tx, kFastExt2.ty, kFastExt2.pfb, kFastExt2.mb, false>(ta, st);
-    return cudaErrorInvalidValue;
-}
+#undef LBM_OWN_CASE
 
 }  // namespace lbm

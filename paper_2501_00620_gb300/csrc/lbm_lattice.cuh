@@ -176,6 +176,9 @@ template <> struct Store<double> {
     using breal = double;
     template <typename I> __device__ __forceinline__ static double ld(const double* p, I k) { return __ldg(p + k); }
     template <typename I> __device__ __forceinline__ static void st(double* p, I k, double v) { p[k] = v; }
+    __device__ __forceinline__ static void stb(double* p, unsigned b, double v) {
+        *reinterpret_cast<double*>(reinterpret_cast<char*>(p) + b) = v;
+    }
 };
 
 template <> struct Store<float> {
@@ -183,6 +186,9 @@ template <> struct Store<float> {
     using breal = float;
     template <typename I> __device__ __forceinline__ static float ld(const float* p, I k) { return __ldg(p + k); }
     template <typename I> __device__ __forceinline__ static void st(float* p, I k, float v) { p[k] = v; }
+    __device__ __forceinline__ static void stb(float* p, unsigned b, float v) {
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(p) + b) = v;
+    }
 };
 
 template <> struct Store<__half> {
@@ -192,6 +198,9 @@ template <> struct Store<__half> {
         return __half2float(__ldg(p + k));
     }
     template <typename I> __device__ __forceinline__ static void st(__half* p, I k, float v) { p[k] = __float2half_rn(v); }
+    __device__ __forceinline__ static void stb(__half* p, unsigned b, float v) {
+        *reinterpret_cast<__half*>(reinterpret_cast<char*>(p) + b) = __float2half_rn(v);
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -202,6 +211,9 @@ template <> struct Store<__nv_bfloat16> {
     }
     template <typename I> __device__ __forceinline__ static void st(__nv_bfloat16* p, I k, float v) {
         p[k] = __float2bfloat16_rn(v);
+    }
+    __device__ __forceinline__ static void stb(__nv_bfloat16* p, unsigned b, float v) {
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(p) + b) = __float2bfloat16_rn(v);
     }
 };
 

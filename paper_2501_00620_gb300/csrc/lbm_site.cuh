@@ -205,9 +205,27 @@ __device__ __forceinline__ void fd_add(int i, const R* rbn, const R* un, R* F, R
 // Where the emitted population i of the site goes: plane i at the site
 // (pull scheme, A-B buffers); the in-place scheme supplies its own map.
 template <typename I> struct PlaneDst {
+    static constexpr bool kBytes = false;
     I s;
     __device__ __forceinline__ I operator()(int i, I N) const { return (I)i * N + s; }
 };
+// The same destination as a 32-bit byte offset from the buffer (plane i at
+// i * pb + sb), for kernels whose population buffers span less than 4 GiB:
+// the per-plane part is block-uniform, the per-site part one register.
+struct PlaneDstBytes {
+    static constexpr bool kBytes = true;
+    unsigned sb, pb;
+    template <typename I> __device__ __forceinline__ unsigned operator()(int i, I) const { return (unsigned)i * pb + sb; }
+};
+template <typename T, typename = void> struct dst_bytes : std::false_type {};
+template <typename T> struct dst_bytes<T, std::void_t<decltype(T::kBytes)>> : std::bool_constant<T::kBytes> {};
+template <typename FS, typename R, typename Dst, typename I>
+__device__ __forceinline__ void store_pop(FS* fo, const Dst& dst, int i, I N, R v) {
+    if constexpr (dst_bytes<Dst>::value)
+        Store<FS>::stb(fo, dst(i, N), v);
+    else
+        Store<FS>::st(fo, dst(i, N), v);
+}
 
 template <int D, typename FS, typename R, typename I = long long, typename Dst = PlaneDst<I>>
 __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R* df, R rho, const R* u,
@@ -263,7 +281,7 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R*
         ev[0] = dr - dm2 + R(2.0 / 3.0) * F0;
         ev[1] = R(0.5) * dm2 + R(1.0 / 6.0) * (F0 + g45[0]);
     }
-    Store<FS>::st(fo, dst(0, N), fma(om1, df[0], omega * ev[0]));
+    store_pop<FS, R>(fo, dst, 0, N, fma(om1, df[0], omega * ev[0]));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int ib = opposite<D>(i);
@@ -274,8 +292,8 @@ __device__ __forceinline__ void collide_store(FS* __restrict__ fo, I N, const R*
             if (L::e(i, c) != 0) eM += R(L::e(i, c)) * mom[c];
         const R A = omega * ev[i];
         const R B = (R(3.0 * L::w(i)) * omega) * eM;
-        Store<FS>::st(fo, dst(i, N), fma(om1, df[i], A + B));
-        Store<FS>::st(fo, dst(ib, N), fma(om1, df[ib], A - B));
+        store_pop<FS, R>(fo, dst, i, N, fma(om1, df[i], A + B));
+        store_pop<FS, R>(fo, dst, ib, N, fma(om1, df[ib], A - B));
     }
 }
 

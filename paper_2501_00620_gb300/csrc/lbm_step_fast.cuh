@@ -113,7 +113,9 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     bool timed_out = false;  // a wait of this thread gave up
     // this thread's region site: wrapped coordinates and source offsets
     int rx = 0, ry = 0, gxw = 0, gyw = 0;
-    int xs[3], ys[3];    // x and y*nx of the sources x - e, y - e for e = -1, 0, 1
+    // byte offsets (population storage) of the sources x - e and rows y - e,
+    // e = -1, 0, 1: x * sizeof(FS) and y * nx * sizeof(FS)
+    int xs[3], ys[3];
     int xo = 0;          // FX: bit e+1 set if source column x - e lies outside [0, nx)
     bool reservoir = false;
     uint32_t tbase = 0;  // TM: TMEM base address of the block
@@ -177,33 +179,38 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
 #pragma unroll
         for (int e = -1; e <= 1; ++e) {
             const int sx = gxw - e;
-            xs[e + 1] = wrap(sx, nx);
+            xs[e + 1] = wrap(sx, nx) * (int)sizeof(FS);
             if (FX && (sx < 0 || sx >= nx)) xo |= 1 << (e + 1);
         }
         gyw = (D == 3) ? wrap(y0 - 1 + ry, ny) : 0;
 #pragma unroll
-        for (int e = -1; e <= 1; ++e) ys[e + 1] = (D == 3) ? wrap(gyw - e, ny) * nx : 0;
+        for (int e = -1; e <= 1; ++e) ys[e + 1] = (D == 3) ? wrap(gyw - e, ny) * nx * (int)sizeof(FS) : 0;
     }
-    // Offsets of the source planes q - e (e = -1, 0, 1) along the march axis.
+    // Byte offsets of the source planes q - e (e = -1, 0, 1) along the march
+    // axis.
     __device__ __forceinline__ void planes(int q, int* zs) const {
 #pragma unroll
-        for (int e = -1; e <= 1; ++e) zs[e + 1] = wrapq(q - e) * pstride;
+        for (int e = -1; e <= 1; ++e) zs[e + 1] = wrapq(q - e) * pstride * (int)sizeof(FS);
     }
 
-    // Pull: df_i = stored deviation of fbar*_i at (x - e_i) (Eq. 49).
+    // Pull: df_i = stored deviation of fbar*_i at (x - e_i) (Eq. 49).  The
+    // address is the block-uniform base of plane i plus a 32-bit byte offset
+    // (one add of three per-thread offsets), not a 64-bit index computation
+    // per population.
     __device__ __forceinline__ void pull(int q, const int* zs, float* df) const {
-        const FS* __restrict__ fin = static_cast<const FS*>(a.fin);
+        const char* __restrict__ fin = static_cast<const char*>(a.fin);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
             const int m = march(i);
-            const int sidx = xs[ex + 1] + ((D == 3) ? ys[ey + 1] : 0) + zs[m + 1];
+            const unsigned off = (unsigned)(xs[ex + 1] + ((D == 3) ? ys[ey + 1] : 0) + zs[m + 1]);
             if (FX && ex != 0 && (xo & (1 << (ex + 1)))) {
                 const float* __restrict__ gf = static_cast<const float*>(a.gf);
                 const int row = (D == 3) ? wrap(gyw - ey, ny) + ny * wrapq(q - ez) : wrapq(q - ey);
                 df[i] = gf[((ex > 0 ? 0 : 1) * Q + i) * (int)a.rows + row];
             } else {
-                df[i] = Store<FS>::ld(fin + i * Ni, sidx);
+                const char* plane = fin + (size_t)i * (size_t)Ni * sizeof(FS);
+                df[i] = Store<FS>::ld(reinterpret_cast<const FS*>(plane + off), 0);
             }
         }
     }
@@ -428,7 +435,8 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
 
     // ---- stage 2: gradients, collision and store of this tile site at plane p ----
     __device__ __forceinline__ void stage2(int p, const int* zsp, DiagDev<D + 2>& acc, int& bad) {
-        const int s = xs[1] + ((D == 3) ? ys[1] : 0) + zsp[1];
+        const unsigned sb = (unsigned)(xs[1] + ((D == 3) ? ys[1] : 0) + zsp[1]);  // byte offset of the site
+        const int s = (int)(sb / sizeof(FS));
         const int rc = rx + RX * ry;
         const float2* am = aux(p - 1);
         const float2* a0 = aux(p);
@@ -493,7 +501,9 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
                     for (int d2 = c; d2 < D; ++d2) G[sym<D>(c, d2)] += ru[c] * ga[d2] + ru[d2] * ga[c];
             }
         }
-        site_collide<D, FS, float, int, DiagDev<D + 2>>(a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad);
+        site_collide<D, FS, float, int, DiagDev<D + 2>, PlaneDstBytes>(
+            a, s, df, c_bt, c_rho, c_j, c_E, F, G, acc, bad, -1.0,
+            PlaneDstBytes{sb, (unsigned)Ni * (unsigned)sizeof(FS)});
         if constexpr (Sh::EXT && D == 3) {
             if (a.mrt && a.write_state) mrt_correct<FS, float>(a, s, df, c_rho, c_j, F);
         }
