@@ -80,6 +80,8 @@ def parse(argv=None):
                    help="skip the short measurements of the other workloads that follow the default "
                         "(turb3d, one GPU) line's own measurement")
     p.add_argument("--requests", type=int, default=1000, help="serve: number of requests of the mix")
+    p.add_argument("--rate", type=float, default=200.0,
+                   help="serve: Poisson arrival rate (requests per second; the mix states 200)")
     p.add_argument("--no-sequential", action="store_true", help="serve: skip the one-at-a-time comparison")
     return p.parse_args(argv)
 
@@ -415,7 +417,7 @@ def run_serve(args):
     from paper_2501_00620_gb300 import lbm
     from paper_2501_00620_gb300 import workloads as W
 
-    reqs = W.serving_requests(args.requests, 200.0, seed=0)
+    reqs = W.serving_requests(args.requests, args.rate, seed=0)
     sites = [r["nx"] * r["ny"] for r in reqs]
     updates = float(sum(n * r["steps"] for n, r in zip(sites, reqs)))
     # the server's precision policy: FP64 storage for 1D fixed-state (Riemann)
@@ -507,7 +509,7 @@ def run_serve(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": len(reqs),
         "warmup": 8, "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (f64 for 1D fixed-state requests)", "data": "synthetic",
-        "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "requests": len(reqs),
+        "config": {"workload": "serve: " + WORKLOAD_TEXT["serve"], "requests": len(reqs), "rate_per_s": args.rate,
                    "site_updates": updates, "step_unit": "one request (steps and ms_per_step count requests)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "kernel": "serve_kernel (persistent cooperative kernel: rounds of K steps posted through a "

@@ -226,9 +226,10 @@ bool tma_applicable(const lbm_sim* s, int v) {
     } else if (generic_only(s)) {
         return false;
     } else if (v >= kPairBase) {
-        // the pair kernel: FP32 storage, periodic lattices
+        // the pair kernel: periodic lattices; FP32 storage, and in 2D also
+        // 16-bit storage
         if (v - kPairBase >= n_pair_variants(s->D)) return false;
-        if (s->dtype != DT_F32 || s->bc != LBM_BC_PERIODIC) return false;
+        if ((s->dtype != DT_F32 && s->D != 2) || s->bc != LBM_BC_PERIODIC) return false;
     } else if (v - kTmaBase >= n_tma_variants(s->D)) {
         return false;
     }

@@ -30,7 +30,7 @@ constexpr int kTmaBase = 100;
 constexpr int kOwnBase = 150;
 
 // kPairBase + k selects the k-th tile of the pair kernel (lbm_step_pair.cuh):
-// FP32 storage, periodic lattices.
+// periodic lattices, FP32 storage (2D: also FP16/BF16).
 constexpr int kPairBase = 200;
 
 // Variant index of the in-place two-pass step (lbm_step_aa.cuh).

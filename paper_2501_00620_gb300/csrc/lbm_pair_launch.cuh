@@ -82,7 +82,7 @@ cudaError_t pair_by_variant(int k, const TmaArgs* ta, TmaBox* box, cudaStream_t 
 }
 #undef LBM_PAIR_CASE
 
-// Defined in lbm_kernels_pair{2,3}.cu (FP32 storage, periodic lattices).
+// Defined in lbm_kernels_pair{2,3}.cu (periodic lattices; FP32 storage, 2D also FP16/BF16).
 int n_pair_variants_d2();
 int n_pair_variants_d3();
 Variant pair_variant_d2(int k);
