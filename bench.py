@@ -40,10 +40,8 @@ WORKLOAD_TEXT = {
     "std3d": "standard-lattice comparator (BGK, Hermite equilibrium of Eq. 4) on D3Q19 256^3 periodic; "
              "the turb3d velocity field (Mach 0.12 at cs2 = 1/3); T0=1/3; tau=0.52",
     "channel3d": "D3Q19 256^3 plane Poiseuille channel: half-way bounce-back walls normal to z, uniform "
-                 "acceleration 1e-7 along x, from rest (rho=1, u=0, T=T0=0.1); tau=0.6; isothermal; "
-                 "generic kernel (walls and force)",
-    "mrt3d": "the turb3d lattice and fields with the MRT collision of Appendix B (s3=1.2, s4=1.4); "
-             "generic kernel",
+                 "acceleration 1e-7 along x, from rest (rho=1, u=0, T=T0=0.1); tau=0.6; isothermal",
+    "mrt3d": "the turb3d lattice and fields with the MRT collision of Appendix B (s3=1.2, s4=1.4)",
     "sound1d": "D1Q3 256 periodic sound wave, rho=1+1e-3 sin(2 pi x/256), T0=1/3, tau=0.8; isothermal",
     "riemann1d": "D1Q3 4096 two-state Riemann (rho 1:0.125, T 1.0:0.8 x 0.15), tau=0.55; thermal; "
                  "fixed-state ends",
@@ -548,7 +546,7 @@ def run_serve(args):
 # (workload, storage, timed steps, warm-up steps).  Each is timed with CUDA
 # events on its own stream after the autotuner has run, like the headline.
 OTHER_WORKLOADS = (("tgv2d", "f32", 50, 5), ("tgv2d", "f16", 50, 5), ("tgv2d", "bf16", 50, 5),
-                   ("std3d", "f32", 40, 5), ("channel3d", "f32", 5, 3), ("mrt3d", "f32", 5, 3),
+                   ("std3d", "f32", 40, 5), ("channel3d", "f32", 40, 5), ("mrt3d", "f32", 40, 5),
                    ("sound1d", "f64", 2000, 5), ("riemann1d", "f64", 5000, 5), ("riemann1d", "f32", 1000, 5))
 
 

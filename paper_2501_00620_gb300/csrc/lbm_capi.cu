@@ -205,11 +205,20 @@ bool ext_ok(const lbm_sim* s) {
     return (s->forced || s->mrt) && s->bc == LBM_BC_PERIODIC && s->dtype == DT_F32 && s->D >= 2 && !small_t_on(s) &&
            s->opts.model == LBM_MODEL_BUMP && !s->opts.inplace;
 }
-bool is_ext_variant(const lbm_sim* s, int v) {
-    return v >= kOwnBase && v < kOwnBase + n_own_variants(s->D) && own_is_ext(s->D, v - kOwnBase);
+// The staged kernel's walls tile serves walled FP32 lattices (with or
+// without force and MRT) without the small-T recovery.
+bool walls_ok(const lbm_sim* s) {
+    return s->bc == LBM_BC_WALLS && s->dtype == DT_F32 && s->D >= 2 && !small_t_on(s) &&
+           s->opts.model == LBM_MODEL_BUMP && !s->opts.inplace && s->opts.halo == 0;
+}
+// 0: not one of the staged kernel's own tiles; 1: force/MRT tile; 2: walls tile
+int own_kind_of(const lbm_sim* s, int v) {
+    return (v >= kOwnBase && v < kOwnBase + n_own_variants(s->D)) ? own_kind(s->D, v - kOwnBase) : 0;
 }
 bool variant_allowed(const lbm_sim* s, int v) {
-    if (is_ext_variant(s, v)) return ext_ok(s);
+    const int kind = own_kind_of(s, v);
+    if (kind == 1) return ext_ok(s);
+    if (kind == 2) return walls_ok(s);
     if (!generic_only(s)) return true;
     return v < kTmaBase && !(s->D == 2 && v == 3);
 }
@@ -219,10 +228,10 @@ bool variant_allowed(const lbm_sim* s, int v) {
 bool tma_applicable(const lbm_sim* s, int v) {
     if (v < kTmaBase || s->D < 2 || s->dtype == DT_F64) return false;
     if (v >= kOwnBase && v < kPairBase) {
-        // FP32, periodic-only tiles: the force/MRT tile for forced or MRT
-        // lattices, the others for plain ones
-        if (v >= kOwnBase + n_own_variants(s->D) || s->dtype != DT_F32 || s->bc != LBM_BC_PERIODIC) return false;
-        if (is_ext_variant(s, v) ? !ext_ok(s) : generic_only(s)) return false;
+        // FP32-only tiles: the force/MRT tile for forced or MRT periodic
+        // lattices, the walls tile for walled ones
+        const int kind = own_kind_of(s, v);
+        if (kind == 0 || (kind == 1 && !ext_ok(s)) || (kind == 2 && !walls_ok(s))) return false;
     } else if (generic_only(s)) {
         return false;
     } else if (v >= kPairBase) {
@@ -603,8 +612,8 @@ lbm_status autotune(lbm_sim* s) {
     // boundary and set of kernels that implement their settings (plain;
     // force or MRT without walls; walls or the small-T recovery).  A forced
     // tile or chunk is not looked up.
-    const int kernels = ext_ok(s) ? 2 : (generic_only(s) ? 1 : 0);
-    auto key = std::make_tuple(s->D, s->dtype * 3 + kernels, (int)s->bc, s->nx, s->ny, s->nz);
+    const int kernels = ext_ok(s) ? 2 : (walls_ok(s) ? 3 : (generic_only(s) ? 1 : 0));
+    auto key = std::make_tuple(s->D, s->dtype * 4 + kernels, (int)s->bc, s->nx, s->ny, s->nz);
     const bool forced_cfg = s->opts.tile >= 0 || s->opts.chunk > 0;
     if (!forced_cfg) {
         std::lock_guard<std::mutex> g(g_tune_mu);

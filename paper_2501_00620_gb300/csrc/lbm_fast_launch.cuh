@@ -23,12 +23,15 @@ struct FastVariant {
 // (the fastest on 256^3).
 constexpr FastVariant kFast3[] = {{32, 8, 0, 2}, {32, 4, 0, 3}, {32, 4, 3, 2}, {32, 4, 1, 3},
                                   {32, 4, 7, 3}};
-// Tiles for FP32 storage and periodic lattices only, instantiated in their
-// own translation unit (lbm_kernels_fastx.cu), variants kOwnBase + k: the
-// fastest D3Q19 and D2Q9 tiles with the body-force and MRT terms in stage 2
-// (PFB bit 3), the kernels of forced or MRT lattices.
-constexpr FastVariant kFastOwn3[] = {{32, 4, 15, 3}};
-constexpr FastVariant kFastOwn2[] = {{128, 1, 15, 6}};
+// Tiles for FP32 storage only, instantiated in their own translation unit
+// (lbm_kernels_fastx.cu), variants kOwnBase + k, on the fastest D3Q19 and
+// D2Q9 tile shapes:
+//  k = 0: the body-force and MRT terms in stage 2 (PFB bit 3): the kernels of
+//         forced or MRT periodic lattices;
+//  k = 1: the same with half-way bounce-back walls normal to the march axis
+//         (PFB bit 4): the kernels of walled lattices.
+constexpr FastVariant kFastOwn3[] = {{32, 4, 15, 3}, {32, 4, 31, 3}};
+constexpr FastVariant kFastOwn2[] = {{128, 1, 15, 6}, {128, 1, 31, 6}};
 // D2Q9: strips of 128 sites; with the populations handed to stage 2 through
 // shared memory; with that hand-off in tensor memory at six blocks per SM.
 constexpr FastVariant kFast2[] = {{128, 1, 0, 5}, {128, 1, 1, 5}, {128, 1, 3, 5}, {128, 1, 7, 6}};

@@ -23,10 +23,11 @@ constexpr int kStripNT = 256;
 // kTmaBase + k selects the k-th tile of the staged kernel (lbm_step_fast.cuh).
 constexpr int kTmaBase = 100;
 
-// kOwnBase + k selects the k-th FP32, periodic-only tile of the staged
-// kernel (lbm_kernels_fastx.cu); k = 0 is the tile with the body-force and
-// MRT terms in stage 2, for lattices with a body force or (D3Q19) the MRT
-// collision.
+// kOwnBase + k selects the k-th FP32-only tile of the staged kernel
+// (lbm_kernels_fastx.cu); own_kind: 1 for the tile with the body-force and
+// MRT terms in stage 2 (periodic lattices with a body force or, D3Q19, the
+// MRT collision), 2 for the tile that adds half-way bounce-back walls
+// (walled lattices, with or without force and MRT).
 constexpr int kOwnBase = 150;
 
 // kPairBase + k selects the k-th tile of the pair kernel (lbm_step_pair.cuh):
@@ -68,7 +69,7 @@ cudaError_t launch_step_multi_d1(int dtype, int v, const StepArgs& a0, const Ste
 cudaError_t launch_step_tma(int D, int dtype, int v, const TmaArgs& ta, cudaStream_t st);
 int n_own_variants(int D);
 Variant own_variant(int D, int k);
-bool own_is_ext(int D, int k);
+int own_kind(int D, int k);
 cudaError_t fast_own(int D, int k, const TmaArgs* ta, TmaBox* box, cudaStream_t st);
 // K steps of a small D2 lattice in one cooperative launch (the generic
 // kernel's strips of kMultiTX2 sites, a0.chunk rows per block).

@@ -61,6 +61,13 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB> struct FastShape 
     static constexpr bool DFS = (PFB & 2) != 0;
     static constexpr bool TM = (PFB & 4) != 0;
     static constexpr bool EXT = (PFB & 8) != 0;
+    // bit 4: half-way bounce-back walls normal to the march axis (StepArgs::
+    // walls, at rest or moving): at the first and last plane the populations
+    // whose source lies beyond a wall are the site's own opposite emissions
+    // (plus the momentum of a moving wall) and carry the site's own
+    // variance; the gradient sees beyond a wall the image of the plane facing
+    // it (same rho b, velocity 2 u_w - u0), as in the generic kernel
+    static constexpr bool WL = (PFB & 16) != 0;
     static constexpr int Q = L::Q, NB = L::NB;
     static constexpr int PXB = 4;                                   // 16-byte aligned x start of a b copy
     static constexpr int SXB = TX + 2 * PXB;                        // sites per staged row
@@ -197,14 +204,42 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     // address is the block-uniform base of plane i plus a 32-bit byte offset
     // (one add of three per-thread offsets), not a 64-bit index computation
     // per population.
-    __device__ __forceinline__ void pull(int q, const int* zs, float* df) const {
+    // WL: wall = 1 at the first plane (sources at q - 1 lie below the lower
+    // wall), 2 at the last (sources at q + 1 above the upper wall), else 0.
+    __device__ __forceinline__ static bool bounced(int wall, int m) {
+        return (wall & 1 && m == 1) || (wall & 2 && m == -1);
+    }
+    __device__ __forceinline__ void pull(int q, const int* zs, float* df, int wall = 0) const {
         const char* __restrict__ fin = static_cast<const char*>(a.fin);
+        // moving walls: density of this site at t, the sum of its emissions
+        float rho_self = 1.0f;
+        if (Sh::WL && wall && a.walls_moving) {
+            const unsigned own = (unsigned)(xs[1] + ((D == 3) ? ys[1] : 0) + zs[1]);
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                rho_self += Store<FS>::ld(
+                    reinterpret_cast<const FS*>(fin + (size_t)k * (size_t)Ni * sizeof(FS) + own), 0);
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
             const int m = march(i);
             const unsigned off = (unsigned)(xs[ex + 1] + ((D == 3) ? ys[ey + 1] : 0) + zs[m + 1]);
-            if (FX && ex != 0 && (xo & (1 << (ex + 1)))) {
+            if (Sh::WL && bounced(wall, m)) {
+                // half-way bounce-back: the site's own opposite emission
+                const unsigned own = (unsigned)(xs[1] + ((D == 3) ? ys[1] : 0) + zs[1]);
+                const char* plane = fin + (size_t)opposite<D>(i) * (size_t)Ni * sizeof(FS);
+                float v = Store<FS>::ld(reinterpret_cast<const FS*>(plane + own), 0);
+                if (a.walls_moving) {
+                    const int side = (wall & 1 && m == 1) ? 0 : 1;
+                    float eu = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < D; ++c)
+                        if (L::e(i, c) != 0) eu += float(L::e(i, c)) * uw_param(a, side, c, 0.0f);
+                    v += 6.0f * float(L::w(i)) * rho_self * eu;
+                }
+                df[i] = v;
+            } else if (FX && ex != 0 && (xo & (1 << (ex + 1)))) {
                 const float* __restrict__ gf = static_cast<const float*>(a.gf);
                 const int row = (D == 3) ? wrap(gyw - ey, ny) + ny * wrapq(q - ez) : wrapq(q - ey);
                 df[i] = gf[((ex > 0 ? 0 : 1) * Q + i) * (int)a.rows + row];
@@ -322,7 +357,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
     // ---- stage 1: pull + moments of this thread's region site at plane q -------
     // Writes (u0, rho b) to the aux plane q; keeps the site values for a tile
     // site.  A fixed-state reservoir site writes the reservoir's aux instead.
-    __device__ __forceinline__ void stage1(int q, const int* zs, bool tile) {
+    __device__ __forceinline__ void stage1(int q, const int* zs, bool tile, int wall = 0) {
         float2* ax = aux(q) + (rx + RX * ry) * NA2;
         if (FX && reservoir) {
             const float* __restrict__ gaux = static_cast<const float*>(a.gaux);
@@ -339,7 +374,7 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             return;
         }
         float df[Q];
-        pull(q, zs, df);
+        pull(q, zs, df, wall);
         const int bo = ((D == 3) ? (ry + 1) * SXB : 0) + (rx - 1 + PXB);
         float bsum[NB];
         if constexpr (D == 3) {
@@ -358,7 +393,9 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
                 const int m = march(i);
                 const int h = (m == 0) ? 0 : 1;
                 const bool first = (i == 0) || (i == 5);  // first in-plane / off-plane source
-                const float2* src = ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
+                // a bounced population carries the site's own variance
+                const float2* src = (Sh::WL && bounced(wall, m)) ? b0
+                                                                 : ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
                 const float fi = float(L::w(i)) + df[i];
                 const float2 f2 = make_float2(fi, fi);
 #pragma unroll
@@ -381,7 +418,8 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             for (int i = 0; i < Q; ++i) {
                 const int offb = -L::e(i, 0);
                 const int m = march(i);
-                const float* src = ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
+                const float* src = (Sh::WL && bounced(wall, m)) ? b0
+                                                                : ((m == 1) ? bm : ((m == -1) ? bp : b0)) + offb;
                 const float fi = float(L::w(i)) + df[i];
                 const float2 f2 = make_float2(fi, fi);
                 const float2 bxy = make_float2(src[0], src[BSLICE]);
@@ -431,6 +469,24 @@ template <int D, typename FS, int TX, int TY, int PFB, int MB, bool FX> struct F
             v[(NB + 1 + D) * NI] = E;
         }
         put_aux<D>(ax, u0, rb);
+    }
+
+    // WL: aux of plane dst, beyond a wall, as the image of this thread's own
+    // site in plane src (same rho b, velocity 2 u_w - u0 of wall `side`).
+    __device__ __forceinline__ void write_image(int src, int dst, int side) const {
+        const float2* as = aux(src) + (rx + RX * ry) * NA2;
+        float2* ad = aux(dst) + (rx + RX * ry) * NA2;
+        float2 g0 = as[0];
+        g0.x = 2.0f * uw_param(a, side, 0, 0.0f) - g0.x;
+        g0.y = 2.0f * uw_param(a, side, 1, 0.0f) - g0.y;
+        ad[0] = g0;
+#pragma unroll
+        for (int k = 1; k < NA2; ++k) ad[k] = as[k];
+        if constexpr (D == 3) {
+            float2 g4 = as[4];
+            g4.x = 2.0f * uw_param(a, side, 2, 0.0f) - g4.x;  // (u_z, rb_zz)
+            ad[4] = g4;
+        }
     }
 
     // ---- stage 2: gradients, collision and store of this tile site at plane p ----
@@ -573,7 +629,22 @@ __device__ __forceinline__ bool fast_segment(const TmaArgs& ta, unsigned char* s
             __syncthreads();
         }
         blk.planes(q, zs);
-        if (interior || ring) blk.stage1(q, zs, interior);
+        if constexpr (Sh::WL) {
+            // walls: nothing lies beyond the lattice along the march axis;
+            // the planes -1 and np hold the images of planes 0 and np - 1
+            const int np = blk.np;
+            if (interior || ring) {
+                if (q >= 0 && q < np) {
+                    const int wall = (q == 0 ? 1 : 0) | (q == np - 1 ? 2 : 0);
+                    blk.stage1(q, zs, interior, wall);
+                    if (q == 0 && p0 == 0) blk.write_image(0, -1, 0);
+                } else if (q == np) {
+                    blk.write_image(np - 1, np, 1);
+                }
+            }
+        } else {
+            if (interior || ring) blk.stage1(q, zs, interior);
+        }
         // The one barrier per plane: aux of plane q is complete and every read
         // of the variance slot of plane q-1 is done.  It also tells every
         // thread at once whether any wait gave up, so all leave together.

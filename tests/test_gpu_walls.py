@@ -140,7 +140,8 @@ def test_force_switches_to_kernels_with_the_force():
     """A forced lattice runs on a kernel that implements the force: setting a
     force on a tuned periodic FP32 lattice re-tunes among the generic kernel
     and the staged kernel's force/MRT tile, and the momentum then grows by
-    M a per step; a walled lattice runs on the generic kernel."""
+    M a per step; a walled lattice whose extents the walls tile does not
+    divide runs on the generic kernel."""
     n = 64
     g = lbm.Simulation(3, n, n, n, tau=0.6, T0=0.1, dtype="f32")
     g.init(1.0, np.zeros((3, n, n, n)), 0.1)
@@ -154,10 +155,10 @@ def test_force_switches_to_kernels_with_the_force():
     assert kernel == "step_kernel" or tile == EXT_TILE
     d1 = g.diagnostics()
     assert np.allclose((d1[1:4] - d0[1:4]) / (10 * d0[0]), acc, rtol=1e-4, atol=1e-9)
-    w = lbm.Simulation(2, 256, 64, tau=0.6, T0=0.1, bc="walls", dtype="f32")
-    w.init(1.0, np.zeros((2, 1, 64, 256)), 0.1)
+    w = lbm.Simulation(2, 250, 64, tau=0.6, T0=0.1, bc="walls", dtype="f32")
+    w.init(1.0, np.zeros((2, 1, 64, 250)), 0.1)
     w.step(1)
-    assert w.launch_config()[2] == "step_kernel"
+    assert w.launch_config()[2] == "step_kernel"  # 250 is no multiple of the walls tile's 128
 
 
 EXT_TILE = 150  # the staged kernel's force/MRT tile
@@ -193,6 +194,66 @@ def test_staged_force_tile_matches_generic_and_oracle(d, shape):
         o.step(1)
         of, ob = o.emitted()
         assert normwise(f1, of) < 2e-6 and np.abs(b1 - ob).max() < 2e-6
+
+
+WALL_TILE = 151  # the staged kernel's walls tile
+
+
+@pytest.mark.parametrize("moving", [False, True])
+@pytest.mark.parametrize("d,shape", [(3, (20, 32, 64)), (3, (9, 16, 96)), (2, (1, 40, 256)), (2, (1, 17, 384))])
+def test_staged_walls_tile_matches_generic_and_oracle(d, shape, moving):
+    """The staged kernel's walls tile (half-way bounce-back at the first and
+    last plane of the march, the site's own variance on bounced populations,
+    image planes beyond the walls for the gradient; a body force; walls at
+    rest or moving): equal to the generic kernel on FP32 storage after
+    several steps, over chunk lengths that do and do not divide the march
+    (chunk ends at the walls and inside); one step from an identical state
+    equal to the FP64 oracle to the FP32 storage precision."""
+    nz, ny, nx = shape
+    rho, u, T = random_fields(d, shape, 41, 0.1)
+    acc = [2e-4, -1e-4, 0.0][:d]
+    # tangential wall velocities: the upper wall moves along x (and y in 3D)
+    uw = ([0.0] * d, [0.02, -0.01, 0.0] if d == 3 else [0.02, 0.0]) if moving else None
+
+    def make(tile, chunk):
+        g = lbm.Simulation(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True, bc="walls", dtype="f32", tile=tile,
+                           chunk=chunk)
+        if uw is not None:
+            g.set_wall_velocity(*uw)
+        g.set_force(acc)
+        g.init(rho, u, T)
+        return g
+
+    ref = make(0, 4)
+    ref.step(7)
+    fr, br = ref.emitted()
+    for chunk in (3, 8):
+        g = make(WALL_TILE, chunk)
+        g.step(6)
+        assert g.launch_config()[0] == WALL_TILE
+        f0, b0 = g.emitted()
+        g.step(1)
+        f1, b1 = g.emitted()
+        assert normwise(f1, fr) < 2e-5 and np.abs(b1 - br).max() < 2e-5
+        o = oracle.Sim(d, nx, ny, nz, tau=0.6, T0=0.1, thermal=True, bc="walls")
+        if uw is not None:
+            o.set_wall_velocity(*uw)
+        o.set_force(acc)
+        o.set_emitted(f0, b0)
+        o.step(1)
+        of, ob = o.emitted()
+        assert normwise(f1, of) < 2e-6 and np.abs(b1 - ob).max() < 2e-6
+
+
+def test_walled_fp32_lattice_tunes_onto_the_walls_tile():
+    """The autotuner times the walls tile beside the generic kernel's tiles
+    for a walled FP32 lattice and keeps the faster (the walls tile on a
+    256 x 64 x 32 channel)."""
+    g = lbm.Simulation(3, 256, 64, 32, tau=0.6, T0=0.1, bc="walls", dtype="f32")
+    g.init(1.0, np.zeros((3, 32, 64, 256)), 0.1)
+    g.set_force([1e-5, 0.0, 0.0])
+    g.step(2)
+    assert g.launch_config()[0] == WALL_TILE
 
 
 @pytest.mark.parametrize("d,shape", [(2, (1, 23, 70)), (3, (13, 11, 37))])
