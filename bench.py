@@ -201,7 +201,7 @@ def hbm_peak():
 
 # the staged kernel's device code (it compiles from these headers alone) and its
 # tile table
-KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_tma.cuh", "lbm_lean.cuh",
+KERNEL_SOURCES = ("lbm_args.cuh", "lbm_lattice.cuh", "lbm_site.cuh", "lbm_tma.cuh", "lbm_lean.cuh", "lbm_mrt.cuh",
                   "lbm_step_fast.cuh", "lbm_fast_launch.cuh")
 
 
