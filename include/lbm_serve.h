@@ -33,7 +33,10 @@
  *    requests join within a round.  Requests of uneven sizes share every
  *    round.  Every wait of the kernel is bounded: after opts.idle_ms without
  *    a posted round (or when the server stops) it leaves, and the service
- *    thread launches it again when work arrives.
+ *    thread launches it again when work arrives.  The kernel holds every
+ *    multiprocessor of the device while it runs: one server per device is
+ *    the intended use (a second server's kernel starts only after the
+ *    first's has left, at the latest idle_ms after its last round).
  *  - A simulation that finishes within a round has its moments computed in
  *    the same round, after its last step; they are copied to host memory
  *    held by the server until lbm_server_poll returns them.  The service
