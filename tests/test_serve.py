@@ -223,3 +223,17 @@ def test_persistent_kernel_leaves_when_idle_and_is_launched_again():
     srv2.close()  # the kernel is waiting for a round: the stop request ends it
     assert time.perf_counter() - t0 < 1.5
     srv.close()
+
+
+def test_close_while_a_round_runs_returns():
+    """Closing a server while its persistent kernel runs a round (a long
+    request in flight) ends the kernel at its next poll: close returns within
+    about one round, and the unfinished request is dropped."""
+    srv = lbm.Server(hbm_budget=1 << 28, idle_ms=5000.0)
+    req = dict(dim=2, nx=512, ny=512, kind="sound", steps=100000)
+    t = submit(srv, req)
+    time.sleep(0.3)  # the kernel is running rounds of the request
+    assert srv.stats()["rounds"] > 0
+    t0 = time.perf_counter()
+    srv.close()
+    assert time.perf_counter() - t0 < 2.0
